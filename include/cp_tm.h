@@ -1,0 +1,144 @@
+/*
+ * cp_tm.h -- C ABI of the GB300 chromatic-polynomial transfer-matrix library.
+ *
+ * Computes P~_G(q) = q^{-|V|} P_G(q) (a polynomial in w = 1/q with constant
+ * term 1, eq. (Z_modified), Sec. 3.5) for L x N rectangles of the square and
+ * triangular lattices with free boundaries, as residues modulo 31-bit primes,
+ * with the sparse per-site transfer matrix of Jacobsen, arXiv:1005.3609:
+ *   P~ = <e_0| T_last T^{N-1} |e_0>,                       eq. (Z_from_T)
+ *   T = T_L ... T_1, per-site factors eqs. (T_sq_proj) / Sec. 3.3,
+ *   T_last = T_L^last ... T_1^last,                         eqs. (T_last), (T_last_i)
+ * acting on vectors indexed by the rank of non-crossing non-nearest-neighbour
+ * (NCNNN) partitions of the L top-row sites (Sec. 3.4).
+ *
+ * Conventions for every entry point:
+ *  - Return CP_OK (0) or a negative status; nothing throws across the ABI.
+ *    The thread-local message of the last failure is cp_last_error().
+ *  - Pointers named *_host are host memory owned by the caller; pointers named
+ *    *_dev are device memory (cudaMalloc/torch) owned by the caller.
+ *  - Library objects (cp_strip, cp_sweep, cp_server) own their device memory
+ *    until the matching destroy call.
+ *  - cuda_stream is a cudaStream_t passed as void*; NULL = legacy default stream.
+ *  - Primes must be distinct primes in [2, 2^31); residues are uint32 < p.
+ *  - Residue arrays of one polynomial are laid out [n_primes][D+1]:
+ *    out[k*(D+1) + j] = coefficient of w^j modulo primes[k].
+ */
+#ifndef CP_TM_H
+#define CP_TM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { CP_SQUARE = 0, CP_TRIANGULAR = 1 };
+
+enum {
+    CP_OK = 0,
+    CP_EINVAL = -1,   /* bad argument                                   */
+    CP_ENOMEM = -2,   /* device or host allocation failed / over budget */
+    CP_ECUDA = -3,    /* a CUDA call failed                             */
+    CP_ETIMEOUT = -4, /* a bounded device wait ran out                  */
+    CP_ESTATE = -5    /* internal consistency check failed              */
+};
+
+#define CP_MAX_L 20       /* widest strip compiled in (the paper's m_max = 20, Sec. 4.2) */
+#define CP_MAX_PRIMES 32
+
+typedef struct cp_strip cp_strip;
+
+/*
+ * cp_create_strip -- a strip of width L, height 1, state vector = e_0.
+ * Builds (or reuses from the per-device cache) the rank tables and the CSR
+ * tables of every per-site factor T_i and T_i^last on the GPU, and allocates
+ * the two state vectors [S][D+1][n_primes] (S = M_{L-1} + M_{L-2} on the
+ * square lattice, M_{L-1} on the triangular one; Sec. 3.2-3.3).
+ *   lattice    CP_SQUARE or CP_TRIANGULAR
+ *   L          1..CP_MAX_L sites per row (strip width m of the paper)
+ *   primes_host, n_primes   1..CP_MAX_PRIMES distinct primes < 2^31 (copied)
+ *   max_degree D >= 0 keeps w^0..w^D (truncation, Sec. 3.5); -1 = full degree
+ *              L*max_rows - 1
+ *   max_rows   height limit (>= 1); advancing beyond it is CP_EINVAL
+ * Errors: CP_EINVAL (bad lattice/L/primes/D), CP_ENOMEM, CP_ECUDA, CP_ESTATE.
+ */
+int cp_create_strip(int lattice, int L, const uint32_t *primes_host, int n_primes,
+                    int max_degree, int max_rows, void *cuda_stream, cp_strip **out);
+
+/*
+ * cp_advance_rows -- apply T = T_L ... T_1 n_rows times (eq. (T_sq_decomp));
+ * height += n_rows.  Asynchronous on the strip's stream (one kernel per site).
+ * Errors: CP_EINVAL (height would exceed max_rows), CP_ECUDA.
+ */
+int cp_advance_rows(cp_strip *s, int n_rows);
+
+/*
+ * cp_read_coeffs -- P~ of the L x height rectangle: applies T_last to a copy
+ * of the state vector and extracts the e_0 coefficient (eqs. (T_last_i),
+ * (Z_from_T)).  Writes out_host[n_primes][D+1] (out_len >= n_primes*(D+1)
+ * words) and *height_out; synchronises the strip's stream.
+ */
+int cp_read_coeffs(cp_strip *s, uint32_t *out_host, size_t out_len, int *height_out);
+
+/* As cp_read_coeffs, into device memory out_dev[n_primes][D+1], asynchronous on
+ * the strip's stream (no host synchronisation). */
+int cp_read_coeffs_device(cp_strip *s, uint32_t *out_dev, size_t out_len);
+
+/* Strip geometry: n_states[0] = NCNNN states S_b, n_states[1] = largest
+ * intermediate space, *degree = D, *height = current height. */
+int cp_strip_info(const cp_strip *s, uint64_t n_states[2], int *degree, int *height);
+
+void cp_destroy(cp_strip *s);
+
+/*
+ * cp_crt -- Chinese remaindering (Sec. 3.5): for each of n_coeffs
+ * coefficients, residues_host[k*n_coeffs + j] modulo primes_host[k] ->
+ * the integer in (-prod/2, prod/2], written as limbs_per_coeff little-endian
+ * 32-bit limbs in two's complement: limbs_host[j*limbs_per_coeff + l].
+ * Runs on the GPU (Garner's mixed radix, one thread per coefficient).
+ * Errors: CP_EINVAL if limbs_per_coeff*32 < bits(prod)+1.
+ */
+int cp_crt(const uint32_t *residues_host, const uint32_t *primes_host, int n_primes,
+           int n_coeffs, uint32_t *limbs_host, int limbs_per_coeff);
+
+/* Device-memory variant of cp_crt (asynchronous on cuda_stream). */
+int cp_crt_device(const uint32_t *residues_dev, const uint32_t *primes_host, int n_primes,
+                  int n_coeffs, uint32_t *limbs_dev, int limbs_per_coeff, void *cuda_stream);
+
+/*
+ * cp_select_primes -- the prime set (Sec. 3.5 leaves the choice open): each
+ * draw in [2^30, 2^31) is mapped on the GPU to the smallest prime >= draw
+ * (deterministic Miller-Rabin, bases 2, 7, 61); repeats and results >= 2^31
+ * are skipped; the first n_primes are written to primes_host.
+ * Errors: CP_EINVAL if the draws yield fewer than n_primes primes.
+ */
+int cp_select_primes(const uint64_t *draws_host, int n_draws, int n_primes, uint32_t *primes_host);
+
+/* Release the per-device cache of transfer-matrix tables (not in use by a
+ * live strip). */
+void cp_clear_table_cache(void);
+
+const char *cp_last_error(void);
+
+/* ---------------------------------------------------------------- diagnostics
+ * Checks of the rank/unrank bijection of Sec. 3.4 on the GPU.
+ * kind 0 = NCNNN partitions of m points (size M_{m-1});
+ * kind 1 = square-lattice space with the pair (e, e+1) excepted (0-based e),
+ *          size M_{m-1} + M_{m-2}, NCNNN ranks first (Sec. 3.4, last paragraph).
+ */
+
+/* For every rank r: unrank, check canonical form and membership, rank again;
+ * *n_bad = number of ranks that fail, *size = size of the space. */
+int cp_debug_check_space(int kind, int m, int e, uint64_t *n_bad, uint64_t *size);
+
+/* Partitions of the space in rank order, as canonical labels:
+ * out_host[r*m + i] = block label of site i (first-occurrence order).
+ * Errors: CP_EINVAL if the space has more than max_states states. */
+int cp_debug_enumerate_space(int kind, int m, int e, uint8_t *out_host, uint64_t max_states, uint64_t *size);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CP_TM_H */

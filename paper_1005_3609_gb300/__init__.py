@@ -1,0 +1,8 @@
+"""GB300-native sparse transfer matrix for the chromatic polynomial (arXiv:1005.3609).
+
+The computation lives in the CUDA library libcp_gb300.so (C ABI in
+include/cp_tm.h); this package is its Python binding.  Importing it does not
+load the library; the first call does, and raises if it is not built.
+"""
+from ._lib import (CP_MAX_L, CP_MAX_PRIMES, CPError, Strip, crt, debug_check_space,  # noqa: F401
+                   debug_enumerate_space, load, select_primes)

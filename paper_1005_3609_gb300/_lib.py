@@ -1,0 +1,181 @@
+"""ctypes binding of libcp_gb300.so (argument marshalling only).
+
+Every computation happens in the CUDA library; this module converts Python
+arguments to the C ABI of include/cp_tm.h and raises on a negative status.
+There is no fallback: if the shared library is missing this raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libcp_gb300.so")
+
+CP_SQUARE, CP_TRIANGULAR = 0, 1
+LATTICES = {"square": CP_SQUARE, "triangular": CP_TRIANGULAR}
+STATUS = {0: "CP_OK", -1: "CP_EINVAL", -2: "CP_ENOMEM", -3: "CP_ECUDA", -4: "CP_ETIMEOUT", -5: "CP_ESTATE"}
+CP_MAX_L = 20
+CP_MAX_PRIMES = 32
+
+u32p = ctypes.POINTER(ctypes.c_uint32)
+u64p = ctypes.POINTER(ctypes.c_uint64)
+vp = ctypes.c_void_p
+
+
+class CPError(RuntimeError):
+    def __init__(self, fn, code, msg):
+        super().__init__("%s -> %s: %s" % (fn, STATUS.get(code, code), msg))
+        self.code = code
+
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "cp_create_strip": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, u32p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       vp, ctypes.POINTER(vp)]),
+    "cp_advance_rows": (ctypes.c_int, [vp, ctypes.c_int]),
+    "cp_read_coeffs": (ctypes.c_int, [vp, u32p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int)]),
+    "cp_read_coeffs_device": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
+    "cp_strip_info": (ctypes.c_int, [vp, u64p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "cp_destroy": (None, [vp]),
+    "cp_crt": (ctypes.c_int, [u32p, u32p, ctypes.c_int, ctypes.c_int, u32p, ctypes.c_int]),
+    "cp_crt_device": (ctypes.c_int, [vp, u32p, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp]),
+    "cp_select_primes": (ctypes.c_int, [u64p, ctypes.c_int, ctypes.c_int, u32p]),
+    "cp_clear_table_cache": (None, []),
+    "cp_last_error": (ctypes.c_char_p, []),
+    "cp_debug_check_space": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, u64p, u64p]),
+    "cp_debug_enumerate_space": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                ctypes.POINTER(ctypes.c_uint8), ctypes.c_uint64, u64p]),
+}
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError("libcp_gb300.so is not built (%s); run __graft_entry__.build()" % path)
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def check(fn, rc):
+    if rc != 0:
+        raise CPError(fn, rc, load().cp_last_error().decode(errors="replace"))
+
+
+def _u32(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.uint32))
+    return a, a.ctypes.data_as(u32p)
+
+
+def lattice_id(lattice):
+    return LATTICES[lattice] if isinstance(lattice, str) else int(lattice)
+
+
+def select_primes(draws, n_primes):
+    d = np.ascontiguousarray(np.asarray(draws, dtype=np.uint64))
+    out = np.zeros(n_primes, dtype=np.uint32)
+    check("cp_select_primes", load().cp_select_primes(d.ctypes.data_as(u64p), len(d), n_primes,
+                                                      out.ctypes.data_as(u32p)))
+    return [int(p) for p in out]
+
+
+def limbs_to_ints(limbs):
+    """Rows of little-endian 32-bit two's-complement limbs -> Python ints."""
+    out = []
+    nl = limbs.shape[1]
+    for row in limbs:
+        v = 0
+        for l in range(nl - 1, -1, -1):
+            v = (v << 32) | int(row[l])
+        if v >> (32 * nl - 1):
+            v -= 1 << (32 * nl)
+        out.append(v)
+    return out
+
+
+def crt(residues, primes, limbs_per_coeff=None):
+    """residues [P][n] -> list of n signed integers (cp_crt)."""
+    res, rp = _u32(residues)
+    pr, pp = _u32(primes)
+    P, n = res.shape
+    if limbs_per_coeff is None:
+        limbs_per_coeff = (31 * P + 2 + 31) // 32 + 1
+    out = np.zeros((n, limbs_per_coeff), dtype=np.uint32)
+    check("cp_crt", load().cp_crt(rp, pp, P, n, out.ctypes.data_as(u32p), limbs_per_coeff))
+    return limbs_to_ints(out)
+
+
+class Strip:
+    """A strip of width L (cp_create_strip / cp_advance_rows / cp_read_coeffs / cp_destroy)."""
+
+    def __init__(self, lattice, L, primes, max_degree=-1, max_rows=1, stream=None):
+        pr, pp = _u32(primes)
+        self.primes = [int(p) for p in pr]
+        h = vp()
+        s = stream if stream is None or isinstance(stream, int) else stream.cuda_stream
+        check("cp_create_strip", load().cp_create_strip(lattice_id(lattice), L, pp, len(pr), max_degree, max_rows,
+                                                        vp(s) if s else None, ctypes.byref(h)))
+        self._h = h
+        ns = (ctypes.c_uint64 * 2)()
+        deg, hgt = ctypes.c_int(), ctypes.c_int()
+        check("cp_strip_info", load().cp_strip_info(h, ns, ctypes.byref(deg), ctypes.byref(hgt)))
+        self.n_states = (int(ns[0]), int(ns[1]))
+        self.degree = deg.value
+        self.L = L
+
+    @property
+    def height(self):
+        deg, hgt = ctypes.c_int(), ctypes.c_int()
+        check("cp_strip_info", load().cp_strip_info(self._h, None, ctypes.byref(deg), ctypes.byref(hgt)))
+        return hgt.value
+
+    def advance(self, n_rows):
+        check("cp_advance_rows", load().cp_advance_rows(self._h, n_rows))
+
+    def read(self):
+        out = np.zeros((len(self.primes), self.degree + 1), dtype=np.uint32)
+        h = ctypes.c_int()
+        check("cp_read_coeffs", load().cp_read_coeffs(self._h, out.ctypes.data_as(u32p), out.size, ctypes.byref(h)))
+        return out
+
+    def read_device(self, ptr, n_words):
+        check("cp_read_coeffs_device", load().cp_read_coeffs_device(self._h, vp(ptr), n_words))
+
+    def close(self):
+        if self._h:
+            load().cp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def debug_check_space(kind, m, e=0):
+    bad, size = ctypes.c_uint64(), ctypes.c_uint64()
+    check("cp_debug_check_space", load().cp_debug_check_space(kind, m, e, ctypes.byref(bad), ctypes.byref(size)))
+    return int(bad.value), int(size.value)
+
+
+def debug_enumerate_space(kind, m, e=0, max_states=1 << 22):
+    buf = np.zeros(max_states * m, dtype=np.uint8)
+    size = ctypes.c_uint64()
+    check("cp_debug_enumerate_space", load().cp_debug_enumerate_space(
+        kind, m, e, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), max_states, ctypes.byref(size)))
+    return buf[: int(size.value) * m].reshape(int(size.value), m)

@@ -1,0 +1,124 @@
+// Internal declarations shared by the translation units of libcp_gb300.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "cp_tm.h"
+
+namespace cp {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+// Distinct primes in [2, 2^31), 1..CP_MAX_PRIMES of them (trial division on the host).
+int check_primes(const uint32_t *primes, int n);
+
+#define CP_CUDA_TRY(expr)                                                                \
+    do {                                                                                 \
+        cudaError_t _e = (expr);                                                         \
+        if (_e != cudaSuccess)                                                           \
+            return ::cp::fail(CP_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+// ------------------------------------------------------------------ state spaces
+// Point counts go up to CP_MAXN in the rank tables (contracted spaces use L-1).
+constexpr int kMaxN = 24;
+constexpr int kTblStride = kMaxN + 1;
+
+// cnt[n] = number of NCNNN partitions of n points (cnt[0] = 1, cnt[n] = M_{n-1});
+// off[n*kTblStride + k] = rank of the first n-point partition whose first point
+// has its smallest partner at relative position 2+k (eq. (M_recurs)).
+struct RankTables {
+    uint64_t cnt[kTblStride];
+    uint64_t off[kTblStride * kTblStride];
+};
+
+// A state space of one per-site factor.
+enum SpaceKind : int32_t { SPACE_B = 0, SPACE_X = 1 };
+struct Space {
+    int32_t kind;   // SPACE_B: NCNNN (first `size` ranks); SPACE_X: pair (e, e+1) excepted
+    int32_t m;      // number of sites
+    int32_t e;      // excepted pair (SPACE_X)
+    int32_t pad;
+    uint64_t size;  // number of ranks used
+};
+
+// Kind of per-site factor.
+enum OpKind : int32_t { OP_SQUARE = 0, OP_TRIANGULAR = 1, OP_LAST = 2, OP_IDENTITY = 3 };
+
+struct OpDesc {
+    int32_t kind;
+    int32_t m;
+    int32_t i;       // 0-based site
+    int32_t max_terms;
+    Space in, out;
+};
+
+// Packed CSR edge: src (27 bits) | shift << 27 (2 bits) | coef << 29 (3-bit two's complement)
+constexpr uint32_t kSrcBits = 27;
+constexpr uint32_t kSrcMask = (1u << kSrcBits) - 1u;
+
+// CSR-by-destination table of one per-site factor, on the device.
+struct SiteTable {
+    OpDesc op;
+    uint64_t n_src = 0, n_dst = 0, nnz = 0;
+    uint32_t *row_ptr = nullptr;  // [n_dst + 1]
+    uint32_t *edges = nullptr;    // [nnz]
+};
+
+// All tables of one (lattice, L) on one device; shared between strips.
+struct TableSet {
+    int device = 0, lattice = 0, L = 0;
+    uint64_t S_b = 0, S_max = 0;
+    std::vector<SiteTable> row;   // T_1..T_L
+    std::vector<SiteTable> last;  // T_1^last..T_{L-1}^last (identity for L = 1)
+    size_t bytes = 0;
+    ~TableSet();
+};
+
+// Rank tables on the current device (built once per device by a kernel).
+int device_rank_tables(const RankTables **out_dev, RankTables *host_copy);
+
+// Build or fetch from the cache the tables of (lattice, L) on the current device.
+int get_tables(int lattice, int L, cudaStream_t stream, std::shared_ptr<TableSet> *out);
+
+// ------------------------------------------------------------------ gather
+// One per-site factor application: out[dst] = sum_e coef_e * w^{shift_e} in[src_e]  (mod p)
+struct GatherTask {
+    const uint32_t *in;
+    uint32_t *out;
+    const uint32_t *row_ptr;
+    const uint32_t *edges;
+    const uint32_t *primes;   // n_primes words, device
+    uint32_t units;           // n_dst * C  (< 2^31; larger factors are split into several tasks)
+    uint32_t C;               // chunks per row
+    uint32_t cpd;             // chunks per degree (= n_primes / VEC)
+    uint32_t vec4;            // 1: 16-byte chunks, 0: 4-byte chunks
+    uint32_t block_begin;     // first block of this task in the launch
+    uint32_t pad[3];
+};
+
+constexpr int kGatherThreads = 256;
+constexpr int kGatherItems = 4;
+constexpr uint32_t kUnitsPerBlock = kGatherThreads * kGatherItems;
+
+// Append the tasks of one per-site factor (split so that each has < 2^31 units).
+void append_gather_tasks(std::vector<GatherTask> *tasks, const SiteTable &tab, const uint32_t *in,
+                         uint32_t *out, const uint32_t *primes_dev, int D1, int P);
+// Launch a batch of tasks (tasks_dev = device copy of tasks_host); block_begin filled by caller.
+int launch_gather(const GatherTask *tasks_dev, int n_tasks, uint32_t total_blocks, cudaStream_t st);
+uint32_t task_blocks(const GatherTask &t);
+
+// Extract the e0 row laid out [D1][P] into [P][D1].
+int launch_transpose_row(const uint32_t *row, uint32_t *out, int D1, int P, cudaStream_t st);
+
+// Device allocation helpers (library-owned memory).
+int dev_alloc(void **p, size_t bytes);
+void dev_free(void *p);
+
+}  // namespace cp

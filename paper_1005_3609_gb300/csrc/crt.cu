@@ -1,0 +1,251 @@
+// Chinese remaindering of the residues (Sec. 3.5) and the prime set.
+//
+// Garner's mixed-radix form x = v_0 + v_1 p_0 + v_2 p_0 p_1 + ..., one thread
+// per coefficient, then Horner in 32-bit limbs and the symmetric
+// representative in (-prod/2, prod/2] as two's complement.
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "cp_internal.h"
+
+namespace cp {
+
+constexpr int kMaxLimbs = 64;
+
+__device__ __forceinline__ uint32_t mulmod(uint32_t a, uint32_t b, uint32_t p) {
+    return (uint32_t)(((uint64_t)a * b) % p);
+}
+
+__device__ uint32_t powmod(uint32_t a, uint32_t e, uint32_t p) {
+    uint32_t r = 1 % p;
+    while (e) {
+        if (e & 1) r = mulmod(r, a, p);
+        a = mulmod(a, a, p);
+        e >>= 1;
+    }
+    return r;
+}
+
+struct CrtParams {
+    uint32_t primes[CP_MAX_PRIMES];
+    int n_primes, n_coeffs, limbs;
+};
+
+// inv[i*P + j] = p_j^{-1} mod p_i (j < i), by Fermat's little theorem.
+__global__ void crt_kernel(const uint32_t *__restrict__ res, uint32_t *__restrict__ limbs_out, CrtParams cp_) {
+    __shared__ uint32_t inv[CP_MAX_PRIMES * CP_MAX_PRIMES];
+    const int P = cp_.n_primes;
+    for (int k = threadIdx.x; k < P * P; k += blockDim.x) {
+        int i = k / P, j = k % P;
+        inv[k] = j < i ? powmod(cp_.primes[j] % cp_.primes[i], cp_.primes[i] - 2, cp_.primes[i]) : 0;
+    }
+    __syncthreads();
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= cp_.n_coeffs) return;
+    uint32_t v[CP_MAX_PRIMES];
+    for (int i = 0; i < P; ++i) {
+        const uint32_t pi = cp_.primes[i];
+        uint32_t t = res[(size_t)i * cp_.n_coeffs + c] % pi;
+        for (int j = 0; j < i; ++j) {
+            uint32_t vj = v[j] % pi;
+            t = t >= vj ? t - vj : t + pi - vj;
+            t = mulmod(t, inv[i * P + j], pi);
+        }
+        v[i] = t;
+    }
+    // x = v_{P-1}; x = x * p_i + v_i for i = P-2..0   (limbs little-endian)
+    uint32_t x[kMaxLimbs], M[kMaxLimbs];
+    const int n = cp_.limbs;
+    for (int l = 0; l < n; ++l) x[l] = M[l] = 0;
+    x[0] = v[P - 1];
+    M[0] = 1;
+    for (int i = P - 2; i >= 0; --i) {
+        uint64_t carry = v[i];
+        for (int l = 0; l < n; ++l) {
+            uint64_t y = (uint64_t)x[l] * cp_.primes[i] + carry;
+            x[l] = (uint32_t)y;
+            carry = y >> 32;
+        }
+    }
+    for (int i = 0; i < P; ++i) {  // M = prod p_i
+        uint64_t carry = 0;
+        for (int l = 0; l < n; ++l) {
+            uint64_t y = (uint64_t)M[l] * cp_.primes[i] + carry;
+            M[l] = (uint32_t)y;
+            carry = y >> 32;
+        }
+    }
+    // if 2x > M: x -= M (two's complement wraps to the negative value)
+    // 2x has limbs (x[l] << 1) | (x[l-1] >> 31) plus the bit x[n-1] >> 31 above the top limb
+    int cmp = (x[n - 1] >> 31) ? 1 : 0;
+    for (int l = n - 1; l >= 0 && cmp == 0; --l) {
+        uint32_t y = (x[l] << 1) | (l > 0 ? x[l - 1] >> 31 : 0u);
+        if (y != M[l]) cmp = y > M[l] ? 1 : -1;
+    }
+    if (cmp > 0) {
+        uint64_t borrow = 0;
+        for (int l = 0; l < n; ++l) {
+            uint64_t y = (uint64_t)x[l] - M[l] - borrow;
+            x[l] = (uint32_t)y;
+            borrow = (y >> 63) & 1;
+        }
+    }
+    for (int l = 0; l < n; ++l) limbs_out[(size_t)c * n + l] = x[l];
+}
+
+static int crt_params(const uint32_t *primes, int P, int n_coeffs, int limbs, CrtParams *cp_) {
+    int rc = check_primes(primes, P);
+    if (rc) return rc;
+    if (n_coeffs < 0) return fail(CP_EINVAL, "n_coeffs < 0");
+    if (limbs < 1 || limbs > kMaxLimbs) return fail(CP_EINVAL, "limbs_per_coeff must be 1..64");
+    double bits = 0;
+    for (int k = 0; k < P; ++k) bits += __builtin_log2((double)primes[k]);
+    if (limbs * 32 < (int)bits + 2) return fail(CP_EINVAL, "limbs_per_coeff too small for the prime product");
+    for (int k = 0; k < P; ++k) cp_->primes[k] = primes[k];
+    cp_->n_primes = P;
+    cp_->n_coeffs = n_coeffs;
+    cp_->limbs = limbs;
+    return CP_OK;
+}
+
+}  // namespace cp
+
+using namespace cp;
+
+extern "C" int cp_crt_device(const uint32_t *res_dev, const uint32_t *primes, int P, int n_coeffs, uint32_t *limbs_dev,
+                             int limbs, void *stream) {
+    CrtParams prm{};
+    int rc = crt_params(primes, P, n_coeffs, limbs, &prm);
+    if (rc) return rc;
+    if (n_coeffs == 0) return CP_OK;
+    if (!res_dev || !limbs_dev) return fail(CP_EINVAL, "NULL argument");
+    crt_kernel<<<(n_coeffs + 63) / 64, 64, 0, (cudaStream_t)stream>>>(res_dev, limbs_dev, prm);
+    CP_CUDA_TRY(cudaGetLastError());
+    return CP_OK;
+}
+
+extern "C" int cp_crt(const uint32_t *res, const uint32_t *primes, int P, int n_coeffs, uint32_t *limbs_out,
+                      int limbs) {
+    CrtParams prm{};
+    int rc = crt_params(primes, P, n_coeffs, limbs, &prm);
+    if (rc) return rc;
+    if (n_coeffs == 0) return CP_OK;
+    if (!res || !limbs_out) return fail(CP_EINVAL, "NULL argument");
+    uint32_t *r_d = nullptr, *l_d = nullptr;
+    if ((rc = dev_alloc((void **)&r_d, 4ull * P * n_coeffs))) return rc;
+    if ((rc = dev_alloc((void **)&l_d, 4ull * limbs * n_coeffs))) {
+        dev_free(r_d);
+        return rc;
+    }
+    cudaError_t e = cudaMemcpy(r_d, res, 4ull * P * n_coeffs, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        crt_kernel<<<(n_coeffs + 63) / 64, 64>>>(r_d, l_d, prm);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(limbs_out, l_d, 4ull * limbs * n_coeffs, cudaMemcpyDeviceToHost);
+    dev_free(r_d);
+    dev_free(l_d);
+    if (e != cudaSuccess) return fail(CP_ECUDA, std::string("cp_crt: ") + cudaGetErrorString(e));
+    return CP_OK;
+}
+
+// ------------------------------------------------------------------ primes
+
+// Deterministic Miller-Rabin for n < 2^32 with bases 2, 7, 61.
+__device__ bool is_prime_u32(uint32_t n) {
+    if (n < 2) return false;
+    const uint32_t small[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 61};
+    for (uint32_t q : small) {
+        if (n == q) return true;
+        if (n % q == 0) return false;
+    }
+    uint32_t d = n - 1;
+    int r = 0;
+    while ((d & 1) == 0) {
+        d >>= 1;
+        ++r;
+    }
+    const uint32_t bases[] = {2, 7, 61};
+    for (uint32_t a : bases) {
+        uint32_t x = powmod(a % n, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool comp = true;
+        for (int k = 1; k < r; ++k) {
+            x = mulmod(x, x, n);
+            if (x == n - 1) {
+                comp = false;
+                break;
+            }
+        }
+        if (comp) return false;
+    }
+    return true;
+}
+
+__global__ void next_prime_kernel(const uint64_t *draws, int n, uint32_t *out) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    uint64_t x = draws[k];
+    uint32_t res = 0;
+    // prime gaps below 2^32 are < 400: a bounded search
+    for (int step = 0; step < 2000 && x < (1ull << 31); ++step, ++x)
+        if (is_prime_u32((uint32_t)x)) {
+            res = (uint32_t)x;
+            break;
+        }
+    out[k] = res;
+}
+
+extern "C" int cp_select_primes(const uint64_t *draws, int n_draws, int n_primes, uint32_t *primes_out) {
+    if (!draws || !primes_out || n_draws < 1 || n_primes < 1) return fail(CP_EINVAL, "bad arguments");
+    uint64_t *d_d = nullptr;
+    uint32_t *o_d = nullptr;
+    int rc = dev_alloc((void **)&d_d, 8ull * n_draws);
+    if (rc) return rc;
+    if ((rc = dev_alloc((void **)&o_d, 4ull * n_draws))) {
+        dev_free(d_d);
+        return rc;
+    }
+    std::vector<uint32_t> cand(n_draws);
+    cudaError_t e = cudaMemcpy(d_d, draws, 8ull * n_draws, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        next_prime_kernel<<<(n_draws + 127) / 128, 128>>>(d_d, n_draws, o_d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(cand.data(), o_d, 4ull * n_draws, cudaMemcpyDeviceToHost);
+    dev_free(d_d);
+    dev_free(o_d);
+    if (e != cudaSuccess) return fail(CP_ECUDA, std::string("cp_select_primes: ") + cudaGetErrorString(e));
+    int k = 0;
+    for (int i = 0; i < n_draws && k < n_primes; ++i) {
+        uint32_t p = cand[i];
+        if (p == 0) continue;
+        bool dup = false;
+        for (int j = 0; j < k; ++j) dup = dup || primes_out[j] == p;
+        if (!dup) primes_out[k++] = p;
+    }
+    if (k < n_primes) return fail(CP_EINVAL, "not enough distinct primes in the draws");
+    return CP_OK;
+}
+
+// ------------------------------------------------------------------ diagnostics
+
+namespace cp {
+int check_space(int kind, int m, int e, uint64_t *n_bad, uint64_t *size);
+int enumerate_space(int kind, int m, int e, uint8_t *out_host, uint64_t max_states, uint64_t *size);
+}  // namespace cp
+
+extern "C" int cp_debug_check_space(int kind, int m, int e, uint64_t *n_bad, uint64_t *size) {
+    if (m < 1 || m > CP_MAX_L || (kind != 0 && kind != 1) || (kind == 1 && (e < 0 || e + 1 >= m)))
+        return fail(CP_EINVAL, "bad space");
+    return check_space(kind, m, e, n_bad, size);
+}
+
+extern "C" int cp_debug_enumerate_space(int kind, int m, int e, uint8_t *out_host, uint64_t max_states,
+                                        uint64_t *size) {
+    if (m < 1 || m > CP_MAX_L || (kind != 0 && kind != 1) || (kind == 1 && (e < 0 || e + 1 >= m)))
+        return fail(CP_EINVAL, "bad space");
+    return enumerate_space(kind, m, e, out_host, max_states, size);
+}

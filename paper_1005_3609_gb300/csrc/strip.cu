@@ -1,0 +1,242 @@
+// cp_strip: one L-wide strip advanced row by row (eq. (Z_from_T)), with the
+// C-ABI entry points declared in cp_tm.h.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cp_internal.h"
+
+namespace cp {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+int dev_alloc(void **p, size_t bytes) {
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? CP_ENOMEM : CP_ECUDA,
+                    "cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+    }
+    return CP_OK;
+}
+
+void dev_free(void *p) {
+    if (p) cudaFree(p);
+}
+
+int check_primes(const uint32_t *primes, int n) {
+    if (!primes || n < 1 || n > CP_MAX_PRIMES) return fail(CP_EINVAL, "n_primes must be 1..CP_MAX_PRIMES");
+    for (int k = 0; k < n; ++k) {
+        uint32_t p = primes[k];
+        if (p < 2 || p >= (1u << 31)) return fail(CP_EINVAL, "prime out of range [2, 2^31)");
+        for (uint32_t d = 2; (uint64_t)d * d <= p; ++d)
+            if (p % d == 0) return fail(CP_EINVAL, "not a prime: " + std::to_string(p));
+        for (int j = 0; j < k; ++j)
+            if (primes[j] == p) return fail(CP_EINVAL, "duplicate prime");
+    }
+    return CP_OK;
+}
+
+}  // namespace cp
+
+using namespace cp;
+
+struct cp_strip {
+    int lattice = 0, L = 0, P = 0, D1 = 0, max_rows = 0, height = 1;
+    cudaStream_t stream = nullptr;
+    std::shared_ptr<TableSet> tabs;
+    uint32_t *primes_dev = nullptr;
+    uint32_t *vec[2] = {nullptr, nullptr};
+    int cur = 0;
+    uint32_t *scratch[2] = {nullptr, nullptr};
+    uint32_t *row_out = nullptr;  // [P][D1]
+    GatherTask *tasks_dev = nullptr;
+    int tasks_cap = 0;
+    // precomputed launches: row factors from vec[0] / vec[1], read-out chain
+    std::vector<std::vector<GatherTask>> row_tasks[2];
+    std::vector<std::vector<GatherTask>> last_tasks[2];
+    std::vector<GatherTask *> row_dev[2], last_dev[2];
+    const uint32_t *last_result[2] = {nullptr, nullptr};
+
+    ~cp_strip() {
+        dev_free(primes_dev);
+        dev_free(vec[0]);
+        dev_free(vec[1]);
+        dev_free(scratch[0]);
+        dev_free(scratch[1]);
+        dev_free(row_out);
+        dev_free(tasks_dev);
+    }
+};
+
+static int upload_tasks(cp_strip *s, std::vector<std::vector<GatherTask>> &lists, std::vector<GatherTask *> &ptrs,
+                        std::vector<GatherTask> &all) {
+    for (auto &l : lists) {
+        uint32_t blk = 0;
+        for (auto &t : l) {
+            t.block_begin = blk;
+            blk += task_blocks(t);
+        }
+        ptrs.push_back(reinterpret_cast<GatherTask *>(all.size()));  // offset, fixed up later
+        all.insert(all.end(), l.begin(), l.end());
+    }
+    return CP_OK;
+}
+
+static uint32_t list_blocks(const std::vector<GatherTask> &l) {
+    uint32_t n = 0;
+    for (auto &t : l) n += task_blocks(t);
+    return n;
+}
+
+extern "C" int cp_create_strip(int lattice, int L, const uint32_t *primes, int n_primes, int max_degree,
+                               int max_rows, void *cuda_stream, cp_strip **out) {
+    if (!out) return fail(CP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (lattice != CP_SQUARE && lattice != CP_TRIANGULAR) return fail(CP_EINVAL, "lattice must be CP_SQUARE or CP_TRIANGULAR");
+    if (L < 1 || L > CP_MAX_L) return fail(CP_EINVAL, "L must be 1..CP_MAX_L");
+    if (max_rows < 1) return fail(CP_EINVAL, "max_rows must be >= 1");
+    if (max_degree < -1) return fail(CP_EINVAL, "max_degree must be >= -1");
+    int rc = check_primes(primes, n_primes);
+    if (rc) return rc;
+    long long D = max_degree >= 0 ? max_degree : (long long)L * max_rows - 1;
+    if (D + 1 > (1 << 20)) return fail(CP_EINVAL, "degree too large");
+    auto s = std::make_unique<cp_strip>();
+    s->lattice = lattice;
+    s->L = L;
+    s->P = n_primes;
+    s->D1 = (int)D + 1;
+    s->max_rows = max_rows;
+    s->stream = (cudaStream_t)cuda_stream;
+    if ((rc = get_tables(lattice, L, s->stream, &s->tabs))) return rc;
+    const TableSet &ts = *s->tabs;
+    const size_t row_words = (size_t)s->D1 * s->P;
+    if ((rc = dev_alloc((void **)&s->primes_dev, 4 * CP_MAX_PRIMES))) return rc;
+    CP_CUDA_TRY(cudaMemcpy(s->primes_dev, primes, 4 * n_primes, cudaMemcpyHostToDevice));
+    for (int k = 0; k < 2; ++k)
+        if ((rc = dev_alloc((void **)&s->vec[k], ts.S_max * row_words * 4))) return rc;
+    // read-out scratch: T_1^last writes cnt[L-1] rows, T_2^last cnt[L-2], ...
+    uint64_t sA = L >= 2 ? ts.last[0].n_dst : 1, sB = L >= 3 ? ts.last[1].n_dst : 1;
+    if ((rc = dev_alloc((void **)&s->scratch[0], sA * row_words * 4))) return rc;
+    if ((rc = dev_alloc((void **)&s->scratch[1], sB * row_words * 4))) return rc;
+    if ((rc = dev_alloc((void **)&s->row_out, row_words * 4))) return rc;
+    // launches of one row (starting from vec[b]) and of the read-out chain from vec[b]
+    std::vector<GatherTask> all;
+    for (int b = 0; b < 2; ++b) {
+        int cur = b;
+        for (int i = 0; i < L; ++i) {
+            std::vector<GatherTask> l;
+            append_gather_tasks(&l, ts.row[i], s->vec[cur], s->vec[cur ^ 1], s->primes_dev, s->D1, s->P);
+            s->row_tasks[b].push_back(l);
+            cur ^= 1;
+        }
+        const uint32_t *src = s->vec[b];
+        int sc = 0;
+        for (size_t i = 0; i < ts.last.size(); ++i) {
+            std::vector<GatherTask> l;
+            append_gather_tasks(&l, ts.last[i], src, s->scratch[sc], s->primes_dev, s->D1, s->P);
+            s->last_tasks[b].push_back(l);
+            src = s->scratch[sc];
+            sc ^= 1;
+        }
+        s->last_result[b] = src;
+        upload_tasks(s.get(), s->row_tasks[b], s->row_dev[b], all);
+        upload_tasks(s.get(), s->last_tasks[b], s->last_dev[b], all);
+    }
+    if ((rc = dev_alloc((void **)&s->tasks_dev, all.size() * sizeof(GatherTask)))) return rc;
+    CP_CUDA_TRY(cudaMemcpy(s->tasks_dev, all.data(), all.size() * sizeof(GatherTask), cudaMemcpyHostToDevice));
+    for (int b = 0; b < 2; ++b) {
+        for (auto &p : s->row_dev[b]) p = s->tasks_dev + reinterpret_cast<size_t>(p);
+        for (auto &p : s->last_dev[b]) p = s->tasks_dev + reinterpret_cast<size_t>(p);
+    }
+    // e_0: rank 0 of the NCNNN space, polynomial 1
+    CP_CUDA_TRY(cudaMemsetAsync(s->vec[0], 0, ts.S_max * row_words * 4, s->stream));
+    std::vector<uint32_t> one(s->P, 1u);
+    CP_CUDA_TRY(cudaMemcpyAsync(s->vec[0], one.data(), 4 * s->P, cudaMemcpyHostToDevice, s->stream));
+    CP_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    s->cur = 0;
+    s->height = 1;
+    *out = s.release();
+    return CP_OK;
+}
+
+extern "C" int cp_advance_rows(cp_strip *s, int n_rows) {
+    if (!s) return fail(CP_EINVAL, "strip is NULL");
+    if (n_rows < 0 || (long long)s->height + n_rows > s->max_rows) return fail(CP_EINVAL, "height would exceed max_rows");
+    for (int r = 0; r < n_rows; ++r) {
+        const int b = s->cur;
+        for (int i = 0; i < s->L; ++i) {
+            int rc = launch_gather(s->row_dev[b][i], (int)s->row_tasks[b][i].size(), list_blocks(s->row_tasks[b][i]),
+                                   s->stream);
+            if (rc) return rc;
+        }
+        s->cur = (b + s->L) & 1;
+        s->height += 1;
+    }
+    return CP_OK;
+}
+
+static int readout(cp_strip *s) {
+    const int b = s->cur;
+    for (size_t i = 0; i < s->last_tasks[b].size(); ++i) {
+        int rc = launch_gather(s->last_dev[b][i], (int)s->last_tasks[b][i].size(),
+                               list_blocks(s->last_tasks[b][i]), s->stream);
+        if (rc) return rc;
+    }
+    return launch_transpose_row(s->last_result[b], s->row_out, s->D1, s->P, s->stream);
+}
+
+extern "C" int cp_read_coeffs_device(cp_strip *s, uint32_t *out_dev, size_t out_len) {
+    if (!s || !out_dev) return fail(CP_EINVAL, "NULL argument");
+    if (out_len < (size_t)s->P * s->D1) return fail(CP_EINVAL, "out_len < n_primes*(D+1)");
+    int rc = readout(s);
+    if (rc) return rc;
+    CP_CUDA_TRY(cudaMemcpyAsync(out_dev, s->row_out, 4ull * s->P * s->D1, cudaMemcpyDeviceToDevice, s->stream));
+    return CP_OK;
+}
+
+extern "C" int cp_read_coeffs(cp_strip *s, uint32_t *out, size_t out_len, int *height_out) {
+    if (!s || !out) return fail(CP_EINVAL, "NULL argument");
+    if (out_len < (size_t)s->P * s->D1) return fail(CP_EINVAL, "out_len < n_primes*(D+1)");
+    int rc = readout(s);
+    if (rc) return rc;
+    CP_CUDA_TRY(cudaMemcpyAsync(out, s->row_out, 4ull * s->P * s->D1, cudaMemcpyDeviceToHost, s->stream));
+    CP_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if (height_out) *height_out = s->height;
+    return CP_OK;
+}
+
+extern "C" int cp_strip_info(const cp_strip *s, uint64_t n_states[2], int *degree, int *height) {
+    if (!s) return fail(CP_EINVAL, "strip is NULL");
+    if (n_states) {
+        n_states[0] = s->tabs->S_b;
+        n_states[1] = s->tabs->S_max;
+    }
+    if (degree) *degree = s->D1 - 1;
+    if (height) *height = s->height;
+    return CP_OK;
+}
+
+extern "C" void cp_destroy(cp_strip *s) {
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream); else cudaDeviceSynchronize();
+    delete s;
+}
+
+extern "C" const char *cp_last_error(void) { return g_err.c_str(); }
+
+namespace cp {
+void clear_table_cache();
+}
+extern "C" void cp_clear_table_cache(void) { cp::clear_table_cache(); }

@@ -1,0 +1,564 @@
+// Transition tables of the per-site factors, built on the GPU.
+//
+// For every source state of a factor's input space: unrank it, apply the
+// factor's single-edge operators (Sec. 3.1-3.3), drop the terms the
+// projectors kill, rank each surviving partition in the output space, and
+// emit (dst, src, shift, coef) terms.  The terms are then counting-sorted by
+// destination into a CSR table, so that the per-site kernel is a gather.
+// Tables depend only on (lattice, L, site): they are built once per device
+// and shared by every strip, row, height and prime.
+#include <cuda_runtime.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <utility>
+
+#include "cp_internal.h"
+#include "ncnnn.cuh"
+
+namespace cp {
+
+// ------------------------------------------------------------------ rank tables
+
+// cnt and off from the recursion M_p = M_{p-1} + sum_{k=0}^{p-2} M_k M_{p-k-2}, eq. (M_recurs).
+__global__ void rank_tables_kernel(RankTables *T) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    uint64_t M[kTblStride];
+    M[0] = 1;
+    M[1] = 1;
+    for (int p = 2; p < kTblStride; ++p) {
+        uint64_t s = M[p - 1];
+        for (int k = 0; k <= p - 2; ++k) s += M[k] * M[p - k - 2];
+        M[p] = s;
+    }
+    T->cnt[0] = 1;
+    for (int n = 1; n < kTblStride; ++n) T->cnt[n] = M[n - 1];
+    for (int k = 0; k < kTblStride * kTblStride; ++k) T->off[k] = 0;
+    for (int n = 3; n < kTblStride; ++n) {
+        uint64_t o = T->cnt[n - 1];
+        for (int k = 0; k <= n - 3; ++k) {
+            T->off[n * kTblStride + k] = o;
+            o += T->cnt[k + 1] * T->cnt[n - k - 2];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ term generation
+
+struct Term {
+    Labels s;
+    int8_t coef;
+    int8_t shift;
+};
+
+constexpr int kMaxTerms = 8;
+
+// H_{a,b} = 1 - J_{a,b} at v = -1: a term with a ~ b is killed (H s = s - s), otherwise
+// it splits into itself and the joined partition with -w.
+__device__ int op_h(Term *t, int n, int m, int a, int b) {
+    int k = n;
+    for (int j = 0; j < n; ++j) {
+        if (t[j].s.v[a] == t[j].s.v[b]) { t[j].coef = 0; continue; }
+        Term u = t[j];
+        join_blocks(u.s, m, a, b);
+        u.coef = (int8_t)-u.coef;
+        u.shift += 1;
+        t[k++] = u;
+    }
+    int w = 0;
+    for (int j = 0; j < k; ++j)
+        if (t[j].coef != 0) t[w++] = t[j];
+    return w;
+}
+
+// V_i = D_i - w.
+__device__ int op_v(Term *t, int n, int m, int i) {
+    for (int j = 0; j < n; ++j) {
+        Term u = t[j];
+        u.coef = (int8_t)-u.coef;
+        u.shift += 1;
+        t[n + j] = u;
+        detach_site(t[j].s, m, i);
+    }
+    return 2 * n;
+}
+
+__device__ int op_d(Term *t, int n, int m, int i) {
+    for (int j = 0; j < n; ++j) detach_site(t[j].s, m, i);
+    return n;
+}
+
+// P_{j,j+1} for j in [lo, hi) except `skip`.
+__device__ int op_p(Term *t, int n, int lo, int hi, int skip) {
+    int w = 0;
+    for (int j = 0; j < n; ++j) {
+        bool ok = true;
+        for (int q = lo; q < hi; ++q)
+            if (q != skip && t[j].s.v[q] == t[j].s.v[q + 1]) { ok = false; break; }
+        if (ok) t[w++] = t[j];
+    }
+    return w;
+}
+
+// Terms of one factor applied to one partition.
+__device__ int factor_terms(const OpDesc &op, const Labels &s, Term *t) {
+    int m = op.m, i = op.i, n = 1;
+    t[0].s = s;
+    t[0].coef = 1;
+    t[0].shift = 0;
+    switch (op.kind) {
+        case OP_SQUARE:  // (prod_{j!=i} P) V_i H_{i,i+1};  T_m = (prod P) V_m      eq. (T_sq_proj)
+            if (i < m - 1) n = op_h(t, n, m, i, i + 1);
+            n = op_v(t, n, m, i);
+            n = op_p(t, n, 0, m - 1, i < m - 1 ? i : -1);
+            break;
+        case OP_TRIANGULAR:  // (prod P) V_i H_{i-1,i} H_{i,i+1}                    Sec. 3.3
+            if (i < m - 1) n = op_h(t, n, m, i, i + 1);
+            if (i > 0) n = op_h(t, n, m, i - 1, i);
+            n = op_v(t, n, m, i);
+            n = op_p(t, n, 0, m - 1, -1);
+            break;
+        case OP_LAST:  // (prod_{j>i} P) D_i H_{i,i+1}                                eq. (T_last_i)
+            if (i < m - 1) n = op_h(t, n, m, i, i + 1);
+            n = op_d(t, n, m, i);
+            n = op_p(t, n, i + 1, m - 1, -1);
+            break;
+        default:  // identity
+            break;
+    }
+    return n;
+}
+
+// One thread per source state.  slot_dst[src*K + t] = destination rank or ~0u,
+// slot_edge[...] = packed edge.  err bits: 1 bad rank / membership, 2 too many
+// terms, 4 coefficient out of range, 8 unrank/rank mismatch of the source.
+__global__ void build_terms_kernel(OpDesc op, const RankTables *Tg, uint32_t *slot_dst, uint32_t *slot_edge,
+                                   int K, int *err) {
+    __shared__ RankTables T;
+    stage_tables(T, Tg);
+    uint64_t src = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (src >= op.in.size) return;
+    Labels s;
+    space_unrank(src, op.in, s, T);
+    int bad = 0;
+    if (!space_contains(s, op.in) || space_rank(s, op.in, T) != src) bad |= 8;
+    Term t[kMaxTerms];
+    int n = factor_terms(op, s, t);
+    uint32_t dst[kMaxTerms];
+    for (int j = 0; j < n; ++j) {
+        if (!space_contains(t[j].s, op.out)) { bad |= 1; dst[j] = ~0u; continue; }
+        uint64_t r = space_rank(t[j].s, op.out, T);
+        if (r >= op.out.size) { bad |= 1; dst[j] = ~0u; continue; }
+        dst[j] = (uint32_t)r;
+    }
+    // merge equal (dst, shift)
+    for (int j = 0; j < n; ++j) {
+        if (t[j].coef == 0 || dst[j] == ~0u) continue;
+        for (int q = j + 1; q < n; ++q)
+            if (dst[q] == dst[j] && t[q].shift == t[j].shift && t[q].coef != 0) {
+                t[j].coef = (int8_t)(t[j].coef + t[q].coef);
+                t[q].coef = 0;
+            }
+    }
+    int w = 0;
+    for (int j = 0; j < n; ++j) {
+        if (t[j].coef == 0 || dst[j] == ~0u) continue;
+        if (t[j].coef < -4 || t[j].coef > 3) { bad |= 4; continue; }
+        if (w >= K) { bad |= 2; break; }
+        slot_dst[src * K + w] = dst[j];
+        slot_edge[src * K + w] = (uint32_t)src | ((uint32_t)t[j].shift << kSrcBits) |
+                                 (((uint32_t)t[j].coef & 7u) << (kSrcBits + 2));
+        ++w;
+    }
+    for (; w < K; ++w) slot_dst[src * K + w] = ~0u;
+    if (bad) atomicOr(err, bad);
+}
+
+// ------------------------------------------------------------------ CSR by destination
+
+__global__ void count_kernel(const uint32_t *slot_dst, uint64_t n_slots, uint32_t *cnt) {
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_slots;
+         k += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t d = slot_dst[k];
+        if (d != ~0u) atomicAdd(&cnt[d], 1u);
+    }
+}
+
+constexpr int kScanThreads = 1024;
+
+// Exclusive scan, three passes: per-block sums, scan of the block sums, per-block scan + offset.
+__device__ __forceinline__ uint32_t block_inclusive_scan(uint32_t v, uint32_t *warp_sums) {
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+    }
+    if (lane == 31) warp_sums[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t x = lane < (int)(blockDim.x >> 5) ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        warp_sums[lane] = x;
+    }
+    __syncthreads();
+    if (wid > 0) v += warp_sums[wid - 1];
+    return v;
+}
+
+__global__ void scan_block_sums(const uint32_t *in, uint64_t n, uint32_t *block_sums) {
+    __shared__ uint32_t ws[32];
+    uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t v = k < n ? in[k] : 0;
+    uint32_t s = block_inclusive_scan(v, ws);
+    if (threadIdx.x == blockDim.x - 1) block_sums[blockIdx.x] = s;
+}
+
+__global__ void scan_sums_serial(uint32_t *sums, uint32_t n_blocks) {
+    // single block: exclusive scan of the block sums in chunks of blockDim
+    __shared__ uint32_t ws[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < n_blocks; base += blockDim.x) {
+        uint32_t k = base + threadIdx.x;
+        uint32_t v = k < n_blocks ? sums[k] : 0;
+        uint32_t inc = block_inclusive_scan(v, ws);
+        uint32_t c = carry;
+        if (k < n_blocks) sums[k] = c + inc - v;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = c + inc;
+        __syncthreads();
+    }
+}
+
+__global__ void scan_finish(const uint32_t *in, uint64_t n, const uint32_t *block_off, uint32_t *out) {
+    __shared__ uint32_t ws[32];
+    uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t v = k < n ? in[k] : 0;
+    uint32_t inc = block_inclusive_scan(v, ws);
+    uint32_t exc = block_off[blockIdx.x] + inc - v;
+    if (k < n) out[k] = exc;
+    if (k == n - 1) out[n] = exc + v;
+}
+
+__global__ void fill_kernel(const uint32_t *slot_dst, const uint32_t *slot_edge, uint64_t n_slots,
+                            const uint32_t *row_ptr, uint32_t *cursor, uint32_t *edges) {
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_slots;
+         k += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t d = slot_dst[k];
+        if (d == ~0u) continue;
+        uint32_t pos = row_ptr[d] + atomicAdd(&cursor[d], 1u);
+        edges[pos] = slot_edge[k];
+    }
+}
+
+// Deterministic order inside each destination: by packed value (src, then shift/coef).
+__global__ void sort_segments_kernel(const uint32_t *row_ptr, uint64_t n_dst, uint32_t *edges) {
+    uint64_t d = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= n_dst) return;
+    uint32_t b = row_ptr[d], e = row_ptr[d + 1];
+    for (uint32_t i = b + 1; i < e; ++i) {
+        uint32_t x = edges[i];
+        uint32_t j = i;
+        while (j > b && edges[j - 1] > x) {
+            edges[j] = edges[j - 1];
+            --j;
+        }
+        edges[j] = x;
+    }
+}
+
+// ------------------------------------------------------------------ host side
+
+static int scan_exclusive(const uint32_t *cnt, uint64_t n, uint32_t *row_ptr, cudaStream_t st) {
+    uint64_t nb = (n + kScanThreads - 1) / kScanThreads;
+    if (nb > (1u << 31)) return fail(CP_EINVAL, "scan too large");
+    uint32_t *sums = nullptr;
+    int rc = dev_alloc((void **)&sums, (nb + 1) * sizeof(uint32_t));
+    if (rc) return rc;
+    scan_block_sums<<<(unsigned)nb, kScanThreads, 0, st>>>(cnt, n, sums);
+    scan_sums_serial<<<1, kScanThreads, 0, st>>>(sums, (uint32_t)nb);
+    scan_finish<<<(unsigned)nb, kScanThreads, 0, st>>>(cnt, n, sums, row_ptr);
+    cudaError_t e = cudaGetLastError();
+    cudaStreamSynchronize(st);
+    dev_free(sums);
+    if (e != cudaSuccess) return fail(CP_ECUDA, std::string("scan: ") + cudaGetErrorString(e));
+    return CP_OK;
+}
+
+static int build_table(const OpDesc &op, const RankTables *T_dev, cudaStream_t st, SiteTable *tab) {
+    tab->op = op;
+    tab->n_src = op.in.size;
+    tab->n_dst = op.out.size;
+    if (op.in.size > kSrcMask || op.out.size >= 0xFFFFFFFFull) return fail(CP_EINVAL, "state space too large");
+    const int K = op.max_terms;
+    uint64_t n_slots = op.in.size * (uint64_t)K;
+    uint32_t *slot_dst = nullptr, *slot_edge = nullptr, *cnt = nullptr, *cursor = nullptr;
+    int *err = nullptr;
+    int rc = CP_OK;
+    auto cleanup = [&]() {
+        dev_free(slot_dst);
+        dev_free(slot_edge);
+        dev_free(cnt);
+        dev_free(cursor);
+        dev_free(err);
+    };
+    if ((rc = dev_alloc((void **)&slot_dst, n_slots * 4)) || (rc = dev_alloc((void **)&slot_edge, n_slots * 4)) ||
+        (rc = dev_alloc((void **)&cnt, op.out.size * 4)) || (rc = dev_alloc((void **)&cursor, op.out.size * 4)) ||
+        (rc = dev_alloc((void **)&err, sizeof(int)))) {
+        cleanup();
+        return rc;
+    }
+    if ((rc = dev_alloc((void **)&tab->row_ptr, (op.out.size + 1) * 4))) {
+        cleanup();
+        return rc;
+    }
+    cudaMemsetAsync(cnt, 0, op.out.size * 4, st);
+    cudaMemsetAsync(cursor, 0, op.out.size * 4, st);
+    cudaMemsetAsync(err, 0, sizeof(int), st);
+    const int bt = 128;
+    build_terms_kernel<<<(unsigned)((op.in.size + bt - 1) / bt), bt, 0, st>>>(op, T_dev, slot_dst, slot_edge, K, err);
+    count_kernel<<<1216, 256, 0, st>>>(slot_dst, n_slots, cnt);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(CP_ECUDA, std::string("build_terms: ") + cudaGetErrorString(e));
+    }
+    if ((rc = scan_exclusive(cnt, op.out.size, tab->row_ptr, st))) {
+        cleanup();
+        return rc;
+    }
+    int herr = 0;
+    uint32_t nnz = 0;
+    cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&nnz, tab->row_ptr + op.out.size, 4, cudaMemcpyDeviceToHost, st);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(CP_ECUDA, std::string("table build: ") + cudaGetErrorString(e));
+    }
+    if (herr) {
+        cleanup();
+        return fail(CP_ESTATE, "transition table check failed (flags " + std::to_string(herr) + ") for op kind " +
+                                   std::to_string(op.kind) + " m=" + std::to_string(op.m) + " i=" +
+                                   std::to_string(op.i));
+    }
+    tab->nnz = nnz;
+    if ((rc = dev_alloc((void **)&tab->edges, (size_t)(nnz ? nnz : 1) * 4))) {
+        cleanup();
+        return rc;
+    }
+    fill_kernel<<<1216, 256, 0, st>>>(slot_dst, slot_edge, n_slots, tab->row_ptr, cursor, tab->edges);
+    sort_segments_kernel<<<(unsigned)((op.out.size + 255) / 256), 256, 0, st>>>(tab->row_ptr, op.out.size, tab->edges);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cleanup();
+    if (e != cudaSuccess) return fail(CP_ECUDA, std::string("csr fill: ") + cudaGetErrorString(e));
+    return CP_OK;
+}
+
+TableSet::~TableSet() {
+    for (auto &t : row) {
+        dev_free(t.row_ptr);
+        dev_free(t.edges);
+    }
+    for (auto &t : last) {
+        dev_free(t.row_ptr);
+        dev_free(t.edges);
+    }
+}
+
+// Identity factor on a 1-state space (T_1^last = D_1 on the width-1 strip).
+static int identity_table(int m, SiteTable *tab) {
+    OpDesc op{};
+    op.kind = OP_IDENTITY;
+    op.m = m;
+    op.in = Space{SPACE_B, m, 0, 0, 1};
+    op.out = op.in;
+    tab->op = op;
+    tab->n_src = tab->n_dst = tab->nnz = 1;
+    int rc = dev_alloc((void **)&tab->row_ptr, 8);
+    if (rc) return rc;
+    if ((rc = dev_alloc((void **)&tab->edges, 4))) return rc;
+    uint32_t rp[2] = {0, 1}, ed = 0u | (1u << (kSrcBits + 2));
+    CP_CUDA_TRY(cudaMemcpy(tab->row_ptr, rp, 8, cudaMemcpyHostToDevice));
+    CP_CUDA_TRY(cudaMemcpy(tab->edges, &ed, 4, cudaMemcpyHostToDevice));
+    return CP_OK;
+}
+
+static int build_tableset(int lattice, int L, cudaStream_t st, std::shared_ptr<TableSet> *out) {
+    const RankTables *T_dev = nullptr;
+    RankTables T;
+    int rc = device_rank_tables(&T_dev, &T);
+    if (rc) return rc;
+    auto ts = std::make_shared<TableSet>();
+    cudaGetDevice(&ts->device);
+    ts->lattice = lattice;
+    ts->L = L;
+    const uint64_t Sb = T.cnt[L];
+    const uint64_t Sx = L >= 2 ? T.cnt[L] + T.cnt[L - 1] : Sb;
+    ts->S_b = Sb;
+    ts->S_max = lattice == CP_SQUARE ? Sx : Sb;
+    for (int i = 0; i < L; ++i) {
+        OpDesc op{};
+        op.m = L;
+        op.i = i;
+        if (lattice == CP_SQUARE) {
+            op.kind = OP_SQUARE;
+            op.max_terms = 4;
+            op.in = i == 0 ? Space{SPACE_B, L, 0, 0, Sb} : Space{SPACE_X, L, i - 1, 0, Sx};
+            op.out = i == L - 1 ? Space{SPACE_B, L, 0, 0, Sb} : Space{SPACE_X, L, i, 0, Sx};
+        } else {
+            op.kind = OP_TRIANGULAR;
+            op.max_terms = 8;
+            op.in = Space{SPACE_B, L, 0, 0, Sb};
+            op.out = op.in;
+        }
+        SiteTable tab;
+        if ((rc = build_table(op, T_dev, st, &tab))) return rc;
+        ts->bytes += (tab.n_dst + 1 + tab.nnz) * 4;
+        ts->row.push_back(tab);
+    }
+    if (L == 1) {
+        SiteTable tab;
+        if ((rc = identity_table(1, &tab))) return rc;
+        ts->last.push_back(tab);
+    } else {
+        for (int i = 0; i + 1 < L; ++i) {  // T_L^last = D_L is the identity on e_0
+            OpDesc op{};
+            op.kind = OP_LAST;
+            op.m = L;
+            op.i = i;
+            op.max_terms = 2;
+            op.in = Space{SPACE_B, L, 0, 0, T.cnt[L - i]};
+            op.out = Space{SPACE_B, L, 0, 0, T.cnt[L - i - 1]};
+            SiteTable tab;
+            if ((rc = build_table(op, T_dev, st, &tab))) return rc;
+            ts->bytes += (tab.n_dst + 1 + tab.nnz) * 4;
+            ts->last.push_back(tab);
+        }
+    }
+    *out = ts;
+    return CP_OK;
+}
+
+static std::mutex g_cache_mu;
+static std::map<std::pair<int, int>, std::shared_ptr<TableSet>> g_cache[64];  // per device
+
+int get_tables(int lattice, int L, cudaStream_t st, std::shared_ptr<TableSet> *out) {
+    int dev = 0;
+    CP_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CP_EINVAL, "device index");
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto key = std::make_pair(lattice, L);
+    auto it = g_cache[dev].find(key);
+    if (it != g_cache[dev].end()) {
+        *out = it->second;
+        return CP_OK;
+    }
+    std::shared_ptr<TableSet> ts;
+    int rc = build_tableset(lattice, L, st, &ts);
+    if (rc) return rc;
+    g_cache[dev][key] = ts;
+    *out = ts;
+    return CP_OK;
+}
+
+void clear_table_cache() {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    for (auto &c : g_cache) c.clear();  // strips keep their own shared_ptr alive
+}
+
+static std::mutex g_rt_mu;
+static RankTables *g_rt_dev[64];
+static RankTables g_rt_host[64];
+
+int device_rank_tables(const RankTables **out_dev, RankTables *host_copy) {
+    int dev = 0;
+    CP_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CP_EINVAL, "device index");
+    std::lock_guard<std::mutex> lk(g_rt_mu);
+    if (!g_rt_dev[dev]) {
+        RankTables *p = nullptr;
+        int rc = dev_alloc((void **)&p, sizeof(RankTables));
+        if (rc) return rc;
+        rank_tables_kernel<<<1, 32>>>(p);
+        CP_CUDA_TRY(cudaGetLastError());
+        CP_CUDA_TRY(cudaMemcpy(&g_rt_host[dev], p, sizeof(RankTables), cudaMemcpyDeviceToHost));
+        g_rt_dev[dev] = p;
+    }
+    *out_dev = g_rt_dev[dev];
+    if (host_copy) *host_copy = g_rt_host[dev];
+    return CP_OK;
+}
+
+// ------------------------------------------------------------------ debug: rank/unrank sweep
+
+__global__ void check_space_kernel(Space sp, const RankTables *Tg, unsigned long long *bad) {
+    __shared__ RankTables T;
+    stage_tables(T, Tg);
+    uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= sp.size) return;
+    Labels s;
+    space_unrank(r, sp, s, T);
+    Labels c = s;
+    canonicalise(c, sp.m);
+    bool ok = space_contains(s, sp) && space_rank(s, sp, T) == r;
+    for (int i = 0; i < sp.m; ++i) ok = ok && c.v[i] == s.v[i];
+    if (!ok) atomicAdd(bad, 1ull);
+}
+
+int check_space(int kind, int m, int e, uint64_t *n_bad, uint64_t *size) {
+    const RankTables *T_dev = nullptr;
+    RankTables T;
+    int rc = device_rank_tables(&T_dev, &T);
+    if (rc) return rc;
+    Space sp{kind, m, e, 0, kind == SPACE_X ? T.cnt[m] + T.cnt[m - 1] : T.cnt[m]};
+    unsigned long long *bad = nullptr;
+    if ((rc = dev_alloc((void **)&bad, 8))) return rc;
+    CP_CUDA_TRY(cudaMemset(bad, 0, 8));
+    check_space_kernel<<<(unsigned)((sp.size + 127) / 128), 128>>>(sp, T_dev, bad);
+    CP_CUDA_TRY(cudaGetLastError());
+    unsigned long long h = 0;
+    CP_CUDA_TRY(cudaMemcpy(&h, bad, 8, cudaMemcpyDeviceToHost));
+    dev_free(bad);
+    *n_bad = h;
+    *size = sp.size;
+    return CP_OK;
+}
+
+// Copy the ranked partitions of a space to the host (labels, m bytes each).
+__global__ void enumerate_kernel(Space sp, const RankTables *Tg, uint8_t *out) {
+    __shared__ RankTables T;
+    stage_tables(T, Tg);
+    uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= sp.size) return;
+    Labels s;
+    space_unrank(r, sp, s, T);
+    for (int i = 0; i < sp.m; ++i) out[r * sp.m + i] = s.v[i];
+}
+
+int enumerate_space(int kind, int m, int e, uint8_t *out_host, uint64_t max_states, uint64_t *size) {
+    const RankTables *T_dev = nullptr;
+    RankTables T;
+    int rc = device_rank_tables(&T_dev, &T);
+    if (rc) return rc;
+    Space sp{kind, m, e, 0, kind == SPACE_X ? T.cnt[m] + T.cnt[m - 1] : T.cnt[m]};
+    *size = sp.size;
+    if (sp.size > max_states) return fail(CP_EINVAL, "output buffer too small");
+    uint8_t *d = nullptr;
+    if ((rc = dev_alloc((void **)&d, sp.size * m))) return rc;
+    enumerate_kernel<<<(unsigned)((sp.size + 127) / 128), 128>>>(sp, T_dev, d);
+    CP_CUDA_TRY(cudaGetLastError());
+    CP_CUDA_TRY(cudaMemcpy(out_host, d, sp.size * m, cudaMemcpyDeviceToHost));
+    dev_free(d);
+    return CP_OK;
+}
+
+}  // namespace cp
