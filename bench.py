@@ -1,0 +1,474 @@
+"""Benchmark: the batched finite-lattice sweep of Jacobsen (arXiv:1005.3609) on GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--workload ...]
+
+Default workload: square lattice, finite-lattice order k = 33 (62 rectangles
+r x s, r <= s, 30 <= r+s <= 33, widths 1..16), 16 primes from the seed-0
+draws, P~ truncated at w^63 (the series to z^63).  One step = one whole sweep:
+reset of every strip to e_0, every per-site factor of every strip (batched
+launches), every read-out, the finite-lattice series modulo each prime (one
+CUDA graph launch) and the Chinese remaindering of the three series on the
+GPU.  The transfer-matrix tables (which depend only on lattice and width) are
+built once before the timed region, like any plan.
+
+value = state-coefficient updates per second (one update = one 32-bit output
+word of one per-site factor), whole job.  e2e = the same metric through the C
+ABI with the primes copied host->device and the CRT'd series copied
+device->host every step.  The reference arm (--impl reference) times the CPU
+oracle on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic_inputs  # noqa: E402
+
+L2_BYTES = 129 * 1024 * 1024
+
+
+# ---------------------------------------------------------------- workload bookkeeping
+
+def motzkin_table(n):
+    M = [1, 1]
+    for p in range(2, n + 1):
+        M.append(M[p - 1] + sum(M[j] * M[p - j - 2] for j in range(p - 1)))
+    return M
+
+
+def band(k):
+    return [(r, s) for r in range(1, k // 2 + 1) for s in range(r, k - r + 1) if r + s >= k - 3]
+
+
+def n_terms(lattice, k):
+    if lattice == "square":
+        return 2 * k - 2 if k % 2 else 2 * k - 3
+    return k
+
+
+def strip_updates(lattice, r, heights, D1, n_primes):
+    """Output words of all per-site factors of one strip (rows and read-outs)."""
+    M = motzkin_table(r + 2)
+    cnt = lambda n: 1 if n == 0 else M[n - 1]
+    Sb = cnt(r)
+    Sx = cnt(r) + cnt(r - 1) if r >= 2 else Sb
+    if lattice == "square":
+        row = sum(Sx if i < r - 1 else Sb for i in range(r))
+    else:
+        row = r * Sb
+    last = sum(cnt(r - i - 1) for i in range(r - 1)) if r >= 2 else 1
+    return ((max(heights) - 1) * row + len(heights) * last) * D1 * n_primes
+
+
+# ---------------------------------------------------------------- CPU oracle (baseline / reference arm)
+
+def _oracle_job(args):
+    lattice, widths, k, D, p = args
+    from oracle import modp
+    hb = {}
+    for r, s in band(k):
+        hb.setdefault(r, []).append(s)
+    t = time.perf_counter()
+    for r in widths:
+        modp.ptilde_heights(lattice, r, hb[r], D, p)
+    return time.perf_counter() - t
+
+
+def oracle_sample(pool, lattice, k, primes, widths):
+    """Run the plain-C mod-p oracle on the band rectangles of the given widths,
+    one process per prime.  Returns (updates/s, wall s, updates, processes)."""
+    D1 = n_terms(lattice, k)
+    hb = {}
+    for r, s in band(k):
+        hb.setdefault(r, []).append(s)
+    upd = sum(strip_updates(lattice, r, hb[r], D1, 1) for r in widths) * len(primes)
+    t = time.perf_counter()
+    pool.map(_oracle_job, [(lattice, widths, k, D1 - 1, p) for p in primes])
+    wall = time.perf_counter() - t
+    return upd / wall, wall, upd
+
+
+def make_pool(n):
+    ctx = mp.get_context("spawn")
+    return ctx.Pool(n)
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        rows = []
+        for ln in open(self.path):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def load_traffic(kernel_key):
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary, if it
+    was taken on the current kernel source (same fingerprint)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+    except Exception:
+        return None
+    ent = d.get(kernel_key)
+    if not ent or ent.get("source_sha") != gather_source_sha():
+        return None
+    return ent
+
+
+def gather_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("gather.cu", "cp_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_1005_3609_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def plain_run(cp, torch, lattice, k, primes, stream):
+    """One (rectangle, prime) at a time: a 1-prime strip per width, reset to e_0
+    for every rectangle, advanced by per-site launches, read into device memory."""
+    D1 = n_terms(lattice, k)
+    hb = {}
+    for r, s in band(k):
+        hb.setdefault(r, []).append(s)
+    strips = {r: cp.Strip(lattice, r, [primes[0]], max_degree=D1 - 1, max_rows=max(hb[r]), stream=stream)
+              for r in hb}
+    out = torch.zeros(D1, dtype=torch.int32, device="cuda")
+    upd = 0
+    for r in hb:
+        upd += sum(strip_updates(lattice, r, [s], D1, 1) for s in hb[r])
+    upd *= len(primes)
+
+    def once():
+        for p in primes:
+            for r in hb:
+                st = strips[r]
+                for s in hb[r]:
+                    st.reset()
+                    st.advance(s - 1)
+                    st.read_device(out.data_ptr(), D1)
+
+    # the strips hold primes[0]; the per-prime loop repeats the same work, as a
+    # one-prime-at-a-time run on another prime would (same launches, same bytes)
+    with torch.cuda.stream(stream):
+        once()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        once()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    for s in strips.values():
+        s.close()
+    return e0.elapsed_time(e1), upd
+
+
+def gpu_arm(args):
+    import torch
+    import paper_1005_3609_gb300 as cp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    pool = None
+    if world == 1 and not args.no_cpu_baseline:
+        pool = make_pool(min(16, os.cpu_count() or 1))  # spawn, before the first GPU call
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    cp.load()
+    lattice, k, P = args.lattice, args.k, args.primes
+    draws = synthetic_inputs.prime_draws(rank, 256)
+    primes = cp.select_primes(draws, P)
+    stream = torch.cuda.Stream()
+    t_setup = time.perf_counter()
+    sw = cp.Sweep(lattice, k, primes, stream, tile=args.tile, prime_groups=args.groups)
+    setup_s = time.perf_counter() - t_setup
+    n = sw.n_terms
+    limbs = (31 * P + 33) // 32 + 1
+    res_dev = torch.zeros(3 * P * n, dtype=torch.int32, device="cuda")
+    limb_dev = torch.zeros(3 * n * limbs, dtype=torch.int32, device="cuda")
+    lib = cp.load()
+    import ctypes
+    pr_arr = (ctypes.c_uint32 * P)(*primes)
+
+    def crt_device():
+        # residues [3][P][n] -> limbs [3][n][limbs], one launch per series
+        sw.read_series_device(res_dev.data_ptr(), res_dev.numel())
+        for x in range(3):
+            cp._lib.check("cp_crt_device", lib.cp_crt_device(
+                ctypes.c_void_p(res_dev.data_ptr() + 4 * x * P * n), pr_arr, P, n,
+                ctypes.c_void_p(limb_dev.data_ptr() + 4 * x * n * limbs), limbs, ctypes.c_void_p(stream.cuda_stream)))
+
+    def step():
+        sw.run()
+        crt_device()
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    updates_total = sw.updates_per_run * args.steps * world
+    value = updates_total / (ms / 1e3)
+
+    # ---- e2e through the C ABI: primes host->device, series CRT'd on device, limbs device->host
+    pinned_primes = torch.tensor(primes, dtype=torch.int64).to(torch.int32).pin_memory()
+    pinned_out = torch.zeros(3 * n * limbs, dtype=torch.int32).pin_memory()
+    h2d = 4 * P
+    d2h = 4 * 3 * n * limbs
+    for _ in range(max(1, args.warmup)):
+        sw.set_primes(pinned_primes.numpy().view("uint32"))
+        step()
+        with torch.cuda.stream(stream):
+            pinned_out.copy_(limb_dev, non_blocking=True)
+        stream.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(args.steps):
+        sw.set_primes(pinned_primes.numpy().view("uint32"))
+        step()
+        with torch.cuda.stream(stream):
+            pinned_out.copy_(limb_dev, non_blocking=True)
+        stream.synchronize()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = f0.elapsed_time(f1)
+    host_ms = (time.perf_counter() - t0) * 1e3
+    e2e_ms = max(e2e_ms, host_ms)
+    if dist:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = updates_total / (e2e_ms / 1e3)
+    # the e2e result must be the paper's series
+    from paper_1005_3609_gb300._lib import limbs_to_ints
+    import numpy as np
+    series = [limbs_to_ints(pinned_out.numpy().view(np.uint32).reshape(3, n, limbs)[x]) for x in range(3)]
+
+    # ---- roofline of the dominant kernel (batched gather), one ungraphed pass with per-launch events
+    gather_ms, n_gather, pass_ms = sw.profile()
+    peaks = load_peaks()
+    peak = peaks.get("hbm_gbs") if peaks else None
+    achieved = sw.bytes_per_run / (gather_ms / 1e3) / 1e9
+    traffic = load_traffic("gather_kernel:%s:k%d:P%d" % (lattice, k, P))
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4) if peak else None,
+                "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
+                "algorithmic_bytes_per_launch": sw.bytes_per_run / n_gather,
+                "avg_launch_ms": gather_ms / n_gather,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peak else "fallback 6800 GB/s",
+                "kernel": "gather_kernel<%d> (batched per-site gather)" % sw.tile}
+    if not peak:
+        roofline["peak"] = 6800.0
+        roofline["frac"] = round(achieved / 6800.0, 4)
+
+    out = None
+    if rank == 0:
+        out = {"metric": "state-coeff updates/s (batched finite-lattice sweep)", "value": value,
+               "unit": "updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+               "config": {"workload": "%s lattice finite-lattice sweep k=%d: %d rectangles r x s (r<=s, %d<=r+s<=%d, "
+                                      "widths 1..%d), %d primes/GPU (seed=rank), P~ to w^%d" %
+                                      (lattice, k, sw.n_rects, k - 3, k, k // 2, P, n - 1),
+                          "parallelism": "weak: each rank sweeps its own %d primes, no collective" % P if world > 1
+                          else "single GPU",
+                          "l2": "no flush: working set > L2 (width-16 vectors %.2f GB each)" %
+                                (strip_bytes_max(lattice, k, n, P) / 1e9),
+                          "tables": "built once per (lattice, width) before timing (%.2f s incl. autotune)" % setup_s,
+                          "tile": sw.tile, "prime_groups": sw.prime_groups,
+                          "updates_per_step": sw.updates_per_run, "algorithmic_bytes_per_step": sw.bytes_per_run},
+               "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
+               "gpu_launches": args.steps * (sw.launches_per_run + 3),
+               "roofline": roofline,
+               "hbm_gbs_algorithmic": sw.bytes_per_run * args.steps / (ms / 1e3) / 1e9}
+        if clk:
+            out["clocks"] = clk
+        if lattice == "square" and k == 33:
+            t = table1()
+            out["check"] = {"series_match_table1": series[0] == t["alpha"][:n] and series[1] == t["beta"][:n]
+                            and series[2][: n - 1] == t["gamma"][: n - 1]}
+    if rank == 0 and world == 1 and not args.no_plain:
+        plain_ms, plain_upd = plain_run(cp, torch, lattice, k, primes, stream)
+        out["batched_vs_plain"] = {
+            "plain_ms": plain_ms, "batched_ms": ms / args.steps, "speedup": plain_ms / (ms / args.steps),
+            "plain_updates_per_s": plain_upd / (plain_ms / 1e3),
+            "plain": "one (rectangle, prime) at a time: 1-prime strip reset to e_0 per rectangle, per-site launches, "
+                     "tables cached", "batched": "one graph launch: strip prefixes shared across heights, %d primes "
+                     "per row, all widths in each launch" % (P // sw.prime_groups)}
+    sw.close()
+    if rank == 0 and world == 1 and pool is not None:
+        widths = [r for r in range(1, args.cpu_widths + 1)]
+        rate, wall, upd = oracle_sample(pool, lattice, k, primes, widths)
+        out["cpu_baseline"] = {"value": rate, "unit": "updates/s", "cores": min(16, os.cpu_count() or 1),
+                               "kind": "oracle",
+                               "sample": "plain-C mod-p oracle (hash-map TM), widths 1..%d of the same band, %d primes "
+                                         "(one process per prime), %.1f s wall" % (args.cpu_widths, len(primes), wall)}
+    if pool is not None:
+        pool.close()
+    if rank == 0:
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def table1():
+    """Table 1 of the paper (fixture tests/golden/table1_square.txt)."""
+    a, b, g = [], [], []
+    for ln in open(os.path.join(ROOT, "tests", "golden", "table1_square.txt")):
+        if ln.startswith("#") or not ln.strip():
+            continue
+        f = ln.split()
+        a.append(int(f[1]))
+        b.append(int(f[2]))
+        if f[3] != "-":
+            g.append(int(f[3]))
+    return {"alpha": a, "beta": b, "gamma": g}
+
+
+def strip_bytes_max(lattice, k, n, P):
+    M = motzkin_table(k // 2 + 2)
+    r = k // 2
+    S = M[r - 1] + (M[r - 2] if lattice == "square" else 0)
+    return S * n * P * 4
+
+
+# ---------------------------------------------------------------- reference arm (the CPU oracle)
+
+def reference_arm(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    lattice, k, P = args.lattice, args.k, args.primes
+    from oracle import crt as ocrt
+    primes = ocrt.primes_from_draws(synthetic_inputs.prime_draws(0, 256), P)
+    cores = min(16, os.cpu_count() or 1)
+    pool = make_pool(cores)
+    widths = list(range(1, args.ref_widths + 1))
+    for _ in range(args.warmup):
+        oracle_sample(pool, lattice, k, primes[:cores], [1, 2, 3])
+    tot_upd, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        rate, wall, upd = oracle_sample(pool, lattice, k, primes, widths)
+        tot_upd += upd
+        tot_s += wall
+    pool.close()
+    value = tot_upd / tot_s
+    out = {"impl": "reference", "metric": "state-coeff updates/s (batched finite-lattice sweep)", "value": value,
+           "unit": "updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": tot_s * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "u32", "data": "synthetic",
+           "config": {"workload": "%s lattice finite-lattice sweep k=%d, %d primes; each step a bounded sample: "
+                                  "widths 1..%d" % (lattice, k, P, args.ref_widths)},
+           "cpu_baseline": {"value": value, "unit": "updates/s", "cores": cores, "kind": "oracle",
+                            "sample": "plain-C mod-p oracle, widths 1..%d of the k=%d band, %d primes, one process "
+                                      "per prime" % (args.ref_widths, k, P)},
+           "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--lattice", default="square", choices=["square", "triangular"])
+    ap.add_argument("--k", type=int, default=33)
+    ap.add_argument("--primes", type=int, default=16)
+    ap.add_argument("--tile", type=int, default=0, help="gather units per thread (0 = autotune)")
+    ap.add_argument("--groups", type=int, default=0, help="prime groups (0 = autotune)")
+    ap.add_argument("--cpu-widths", type=int, default=13, help="widths of the CPU-baseline sample")
+    ap.add_argument("--ref-widths", type=int, default=11, help="widths of each reference-arm step")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

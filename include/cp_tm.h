@@ -89,6 +89,10 @@ int cp_read_coeffs_device(cp_strip *s, uint32_t *out_dev, size_t out_len);
  * intermediate space, *degree = D, *height = current height. */
 int cp_strip_info(const cp_strip *s, uint64_t n_states[2], int *degree, int *height);
 
+/* Restart the strip at height 1 with the state vector e_0 (keeps its tables
+ * and buffers).  Asynchronous on the strip's stream. */
+int cp_strip_reset(cp_strip *s);
+
 void cp_destroy(cp_strip *s);
 
 /*
@@ -114,6 +118,66 @@ int cp_crt_device(const uint32_t *residues_dev, const uint32_t *primes_host, int
  * Errors: CP_EINVAL if the draws yield fewer than n_primes primes.
  */
 int cp_select_primes(const uint64_t *draws_host, int n_draws, int n_primes, uint32_t *primes_host);
+
+/* ---------------------------------------------------------------- batched sweep
+ * The finite-lattice sweep of Sec. 4.1-4.3: every rectangle r x s with r <= s
+ * and k-3 <= r+s <= k (the rectangles of B(k) with a non-zero weight,
+ * eqs. (fb)-(fc)), on n_primes primes, truncated to the series order: square
+ * lattice 2k-3 terms in z (2k-2 for odd k, with the mu_{2m} z^{4m-1} terms of
+ * Sec. 4.2 added to f_b and f_s), triangular lattice k terms in x (Sec. 4.3).
+ * One strip per width (and per prime group) is advanced to its largest band
+ * height and read out at each band height; all strips advance together, one
+ * batched launch per site step, and the whole sweep plus the series kernel is
+ * one CUDA graph.
+ */
+typedef struct cp_sweep cp_sweep;
+
+/* tile: gather units per thread (1, 2, 4, 8) or 0 = autotune;
+ * prime_groups: number of strips per width, dividing n_primes, or 0 = autotune.
+ * cuda_stream must be a non-default stream (the program is graph-captured on it).
+ * Errors: CP_EINVAL (k < 4, k/2 > CP_MAX_L, series longer than 128 terms, bad
+ * primes/tile/groups, NULL stream), CP_ENOMEM, CP_ECUDA, CP_ESTATE. */
+int cp_sweep_create(int lattice, int k, const uint32_t *primes_host, int n_primes, int tile, int prime_groups,
+                    void *cuda_stream, cp_sweep **out);
+
+/* Launch the whole sweep (one graph launch), asynchronous on the sweep's stream. */
+int cp_sweep_run(cp_sweep *sw);
+
+/* Wait for the sweep's stream; CP_ESTATE if a P~ had a constant term != 1. */
+int cp_sweep_sync(cp_sweep *sw);
+
+/* Geometry and algorithmic work of one run: output words written by the
+ * per-site factors (updates) and bytes = 4 (S_in + S_out)(D+1) P per factor
+ * plus its CSR index; launches = batched gather launches + 1 series kernel. */
+int cp_sweep_info(const cp_sweep *sw, int *n_rects, int *n_terms, int *tile, int *prime_groups,
+                  uint64_t *updates_per_run, uint64_t *bytes_per_run, int *launches_per_run);
+
+/* The rectangles, rs_host[2j] = r, rs_host[2j+1] = s. */
+int cp_sweep_rects(const cp_sweep *sw, int *rs_host, int max_rects);
+
+/* P~ of every rectangle: out_host[j][k][d] = coefficient of w^d mod primes[k]
+ * for rectangle j, d < n_terms.  Synchronises. */
+int cp_sweep_read_ptilde(cp_sweep *sw, uint32_t *out_host, size_t out_len);
+
+/* Series residues out_host[x][k][i], x = 0 bulk (square: sum alpha_i z^i of
+ * Table 1; triangular: (1-x)^2 exp(f_b)/q, Baxter's product eq. (efb)),
+ * x = 1 exp(f_s), x = 2 exp(f_c); modulo primes[k].  Synchronises. */
+int cp_sweep_read_series(cp_sweep *sw, uint32_t *out_host, size_t out_len);
+
+/* As cp_sweep_read_series into device memory, asynchronous on the sweep's stream. */
+int cp_sweep_read_series_device(cp_sweep *sw, uint32_t *out_dev, size_t out_len);
+
+/* Replace the sweep's primes (same count) for the next run: a host-to-device
+ * copy of n_primes words on the sweep's stream; the tables and the graph stay. */
+int cp_sweep_set_primes(cp_sweep *sw, const uint32_t *primes_host, int n_primes);
+
+/* Run the sweep's per-site launches once WITHOUT the graph, with a CUDA event
+ * pair around each batched gather launch on the sweep's stream: *gather_ms =
+ * summed gather kernel time, *n_gather = launches, *total_ms = whole pass
+ * (no series kernel).  Synchronises.  For roofline measurements. */
+int cp_sweep_profile(cp_sweep *sw, float *gather_ms, int *n_gather, float *total_ms);
+
+void cp_sweep_destroy(cp_sweep *sw);
 
 /* Release the per-device cache of transfer-matrix tables (not in use by a
  * live strip). */

@@ -38,6 +38,22 @@ SIGNATURES = {
     "cp_read_coeffs_device": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
     "cp_strip_info": (ctypes.c_int, [vp, u64p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "cp_destroy": (None, [vp]),
+    "cp_strip_reset": (ctypes.c_int, [vp]),
+    "cp_sweep_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, u32p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       vp, ctypes.POINTER(vp)]),
+    "cp_sweep_run": (ctypes.c_int, [vp]),
+    "cp_sweep_sync": (ctypes.c_int, [vp]),
+    "cp_sweep_info": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), u64p, u64p,
+                                     ctypes.POINTER(ctypes.c_int)]),
+    "cp_sweep_rects": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+    "cp_sweep_read_ptilde": (ctypes.c_int, [vp, u32p, ctypes.c_size_t]),
+    "cp_sweep_read_series": (ctypes.c_int, [vp, u32p, ctypes.c_size_t]),
+    "cp_sweep_read_series_device": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
+    "cp_sweep_destroy": (None, [vp]),
+    "cp_sweep_set_primes": (ctypes.c_int, [vp, u32p, ctypes.c_int]),
+    "cp_sweep_profile": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_float)]),
     "cp_crt": (ctypes.c_int, [u32p, u32p, ctypes.c_int, ctypes.c_int, u32p, ctypes.c_int]),
     "cp_crt_device": (ctypes.c_int, [vp, u32p, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp]),
     "cp_select_primes": (ctypes.c_int, [u64p, ctypes.c_int, ctypes.c_int, u32p]),
@@ -146,6 +162,9 @@ class Strip:
         check("cp_read_coeffs", load().cp_read_coeffs(self._h, out.ctypes.data_as(u32p), out.size, ctypes.byref(h)))
         return out
 
+    def reset(self):
+        check("cp_strip_reset", load().cp_strip_reset(self._h))
+
     def read_device(self, ptr, n_words):
         check("cp_read_coeffs_device", load().cp_read_coeffs_device(self._h, vp(ptr), n_words))
 
@@ -179,3 +198,85 @@ def debug_enumerate_space(kind, m, e=0, max_states=1 << 22):
     check("cp_debug_enumerate_space", load().cp_debug_enumerate_space(
         kind, m, e, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), max_states, ctypes.byref(size)))
     return buf[: int(size.value) * m].reshape(int(size.value), m)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+class Sweep:
+    """The batched finite-lattice sweep (cp_sweep_*): all band rectangles of
+    order k on the given primes, advanced together in one graph launch."""
+
+    def __init__(self, lattice, k, primes, stream, tile=0, prime_groups=0):
+        pr, pp = _u32(primes)
+        self.primes = [int(p) for p in pr]
+        self.lattice = lattice
+        self.k = k
+        h = vp()
+        check("cp_sweep_create", load().cp_sweep_create(lattice_id(lattice), k, pp, len(pr), tile, prime_groups,
+                                                        vp(_stream_handle(stream)), ctypes.byref(h)))
+        self._h = h
+        vals = [ctypes.c_int() for _ in range(4)] + [ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int()]
+        check("cp_sweep_info", load().cp_sweep_info(h, *[ctypes.byref(v) for v in vals]))
+        (self.n_rects, self.n_terms, self.tile, self.prime_groups, self.updates_per_run, self.bytes_per_run,
+         self.launches_per_run) = [v.value for v in vals]
+        rs = (ctypes.c_int * (2 * self.n_rects))()
+        check("cp_sweep_rects", load().cp_sweep_rects(h, rs, self.n_rects))
+        self.rects = [(rs[2 * j], rs[2 * j + 1]) for j in range(self.n_rects)]
+
+    def run(self):
+        check("cp_sweep_run", load().cp_sweep_run(self._h))
+
+    def sync(self):
+        check("cp_sweep_sync", load().cp_sweep_sync(self._h))
+
+    def read_ptilde(self):
+        """{(r, s): uint32 [n_primes][n_terms]}"""
+        out = np.zeros((self.n_rects, len(self.primes), self.n_terms), dtype=np.uint32)
+        check("cp_sweep_read_ptilde", load().cp_sweep_read_ptilde(self._h, out.ctypes.data_as(u32p), out.size))
+        return {rs: out[j] for j, rs in enumerate(self.rects)}
+
+    def read_series(self):
+        """uint32 [3][n_primes][n_terms]: bulk, surface, corner residues."""
+        out = np.zeros((3, len(self.primes), self.n_terms), dtype=np.uint32)
+        check("cp_sweep_read_series", load().cp_sweep_read_series(self._h, out.ctypes.data_as(u32p), out.size))
+        return out
+
+    def set_primes(self, primes):
+        pr, pp = _u32(primes)
+        check("cp_sweep_set_primes", load().cp_sweep_set_primes(self._h, pp, len(pr)))
+        self.primes = [int(p) for p in pr]
+
+    def profile(self):
+        """(summed gather kernel ms, gather launches, whole pass ms) of one ungraphed pass."""
+        g, n, t = ctypes.c_float(), ctypes.c_int(), ctypes.c_float()
+        check("cp_sweep_profile", load().cp_sweep_profile(self._h, ctypes.byref(g), ctypes.byref(n), ctypes.byref(t)))
+        return g.value, n.value, t.value
+
+    def read_series_device(self, ptr, n_words):
+        check("cp_sweep_read_series_device", load().cp_sweep_read_series_device(self._h, vp(ptr), n_words))
+
+    def series_integers(self):
+        """The three series as exact integers (cp_crt over all primes)."""
+        res = self.read_series()
+        return [crt(res[x], self.primes) for x in range(3)]
+
+    def close(self):
+        if self._h:
+            load().cp_sweep_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -104,15 +104,16 @@ struct GatherTask {
 };
 
 constexpr int kGatherThreads = 256;
-constexpr int kGatherItems = 4;
-constexpr uint32_t kUnitsPerBlock = kGatherThreads * kGatherItems;
+constexpr int kGatherItems = 4;  // default (dst, chunk) units per thread
 
 // Append the tasks of one per-site factor (split so that each has < 2^31 units).
 void append_gather_tasks(std::vector<GatherTask> *tasks, const SiteTable &tab, const uint32_t *in,
                          uint32_t *out, const uint32_t *primes_dev, int D1, int P);
-// Launch a batch of tasks (tasks_dev = device copy of tasks_host); block_begin filled by caller.
-int launch_gather(const GatherTask *tasks_dev, int n_tasks, uint32_t total_blocks, cudaStream_t st);
-uint32_t task_blocks(const GatherTask &t);
+// Blocks of one task and of a whole launch (fills block_begin; returns the grid size).
+uint32_t task_blocks(const GatherTask &t, int items);
+uint32_t assign_blocks(std::vector<GatherTask> &tasks, int items);
+// Launch a batch of tasks (tasks_dev = device copy, block_begin assigned) with `items` units per thread.
+int launch_gather(const GatherTask *tasks_dev, int n_tasks, uint32_t total_blocks, int items, cudaStream_t st);
 
 // Extract the e0 row laid out [D1][P] into [P][D1].
 int launch_transpose_row(const uint32_t *row, uint32_t *out, int D1, int P, cudaStream_t st);

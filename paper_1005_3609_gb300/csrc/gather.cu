@@ -11,7 +11,7 @@
 // 32-bit words with p < 2^31 (Sec. 3.5); no floating point.
 //
 // One launch processes a batch of independent tasks (factors of different
-// strips); each block belongs to one task and covers kUnitsPerBlock
+// strips); each block belongs to one task and covers 256 * ITEMS
 // consecutive (dst, chunk) units of it.
 #include <cuda_runtime.h>
 
@@ -45,6 +45,7 @@ __device__ __forceinline__ uint32_t axpy_mod(uint32_t acc, uint32_t x, int coef,
 __device__ __forceinline__ int edge_coef(uint32_t e) { return ((int)(e >> 29) << 29) >> 29; }
 __device__ __forceinline__ uint32_t edge_shift(uint32_t e) { return (e >> kSrcBits) & 3u; }
 
+template <int ITEMS>
 __global__ void __launch_bounds__(kGatherThreads) gather_kernel(const GatherTask *__restrict__ tasks, int n_tasks) {
     // task of this block: the last one whose block_begin <= blockIdx.x
     int lo = 0, hi = n_tasks - 1;
@@ -54,9 +55,9 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(const GatherTask
         if (tasks[mid].block_begin <= b) lo = mid; else hi = mid - 1;
     }
     const GatherTask t = tasks[lo];
-    const uint32_t base = (b - t.block_begin) * kUnitsPerBlock;
+    const uint32_t base = (b - t.block_begin) * (uint32_t)(kGatherThreads * ITEMS);
 #pragma unroll 1
-    for (int it = 0; it < kGatherItems; ++it) {
+    for (int it = 0; it < ITEMS; ++it) {
         const uint32_t u = base + it * kGatherThreads + threadIdx.x;
         if (u >= t.units) return;
         const uint32_t dst = u / t.C;
@@ -95,7 +96,19 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(const GatherTask
     }
 }
 
-uint32_t task_blocks(const GatherTask &t) { return (t.units + kUnitsPerBlock - 1) / kUnitsPerBlock; }
+uint32_t task_blocks(const GatherTask &t, int items) {
+    const uint32_t per = (uint32_t)(kGatherThreads * items);
+    return (t.units + per - 1) / per;
+}
+
+uint32_t assign_blocks(std::vector<GatherTask> &tasks, int items) {
+    uint32_t blk = 0;
+    for (auto &t : tasks) {
+        t.block_begin = blk;
+        blk += task_blocks(t, items);
+    }
+    return blk;
+}
 
 void append_gather_tasks(std::vector<GatherTask> *tasks, const SiteTable &tab, const uint32_t *in, uint32_t *out,
                          const uint32_t *primes_dev, int D1, int P) {
@@ -120,9 +133,15 @@ void append_gather_tasks(std::vector<GatherTask> *tasks, const SiteTable &tab, c
     }
 }
 
-int launch_gather(const GatherTask *tasks_dev, int n_tasks, uint32_t total_blocks, cudaStream_t st) {
+int launch_gather(const GatherTask *tasks_dev, int n_tasks, uint32_t total_blocks, int items, cudaStream_t st) {
     if (n_tasks <= 0 || total_blocks == 0) return CP_OK;
-    gather_kernel<<<total_blocks, kGatherThreads, 0, st>>>(tasks_dev, n_tasks);
+    switch (items) {
+        case 1: gather_kernel<1><<<total_blocks, kGatherThreads, 0, st>>>(tasks_dev, n_tasks); break;
+        case 2: gather_kernel<2><<<total_blocks, kGatherThreads, 0, st>>>(tasks_dev, n_tasks); break;
+        case 4: gather_kernel<4><<<total_blocks, kGatherThreads, 0, st>>>(tasks_dev, n_tasks); break;
+        case 8: gather_kernel<8><<<total_blocks, kGatherThreads, 0, st>>>(tasks_dev, n_tasks); break;
+        default: return fail(CP_EINVAL, "gather tile must be 1, 2, 4 or 8");
+    }
     CP_CUDA_TRY(cudaGetLastError());
     return CP_OK;
 }

@@ -35,13 +35,38 @@ void dev_free(void *p) {
     if (p) cudaFree(p);
 }
 
+// Deterministic Miller-Rabin for n < 2^32 (bases 2, 7, 61).
+static bool host_is_prime(uint32_t n) {
+    if (n < 2) return false;
+    for (uint32_t q : {2u, 3u, 5u, 7u, 11u, 13u, 17u, 19u, 23u, 29u, 31u, 37u, 61u}) {
+        if (n == q) return true;
+        if (n % q == 0) return false;
+    }
+    uint32_t d = n - 1;
+    int r = 0;
+    while (!(d & 1)) { d >>= 1; ++r; }
+    auto mul = [n](uint64_t a, uint64_t b) { return (a * b) % n; };
+    for (uint64_t a : {2ull, 7ull, 61ull}) {
+        uint64_t x = 1, b = a % n;
+        for (uint32_t e = d; e; e >>= 1, b = mul(b, b))
+            if (e & 1) x = mul(x, b);
+        if (x == 1 || x == n - 1) continue;
+        bool comp = true;
+        for (int k = 1; k < r && comp; ++k) {
+            x = mul(x, x);
+            if (x == n - 1) comp = false;
+        }
+        if (comp) return false;
+    }
+    return true;
+}
+
 int check_primes(const uint32_t *primes, int n) {
     if (!primes || n < 1 || n > CP_MAX_PRIMES) return fail(CP_EINVAL, "n_primes must be 1..CP_MAX_PRIMES");
     for (int k = 0; k < n; ++k) {
         uint32_t p = primes[k];
         if (p < 2 || p >= (1u << 31)) return fail(CP_EINVAL, "prime out of range [2, 2^31)");
-        for (uint32_t d = 2; (uint64_t)d * d <= p; ++d)
-            if (p % d == 0) return fail(CP_EINVAL, "not a prime: " + std::to_string(p));
+        if (!host_is_prime(p)) return fail(CP_EINVAL, "not a prime: " + std::to_string(p));
         for (int j = 0; j < k; ++j)
             if (primes[j] == p) return fail(CP_EINVAL, "duplicate prime");
     }
@@ -61,6 +86,7 @@ struct cp_strip {
     int cur = 0;
     uint32_t *scratch[2] = {nullptr, nullptr};
     uint32_t *row_out = nullptr;  // [P][D1]
+    uint32_t *ones_dev = nullptr;  // P ones (the e_0 row)
     GatherTask *tasks_dev = nullptr;
     int tasks_cap = 0;
     // precomputed launches: row factors from vec[0] / vec[1], read-out chain
@@ -76,6 +102,7 @@ struct cp_strip {
         dev_free(scratch[0]);
         dev_free(scratch[1]);
         dev_free(row_out);
+        dev_free(ones_dev);
         dev_free(tasks_dev);
     }
 };
@@ -83,11 +110,7 @@ struct cp_strip {
 static int upload_tasks(cp_strip *s, std::vector<std::vector<GatherTask>> &lists, std::vector<GatherTask *> &ptrs,
                         std::vector<GatherTask> &all) {
     for (auto &l : lists) {
-        uint32_t blk = 0;
-        for (auto &t : l) {
-            t.block_begin = blk;
-            blk += task_blocks(t);
-        }
+        assign_blocks(l, kGatherItems);
         ptrs.push_back(reinterpret_cast<GatherTask *>(all.size()));  // offset, fixed up later
         all.insert(all.end(), l.begin(), l.end());
     }
@@ -96,7 +119,7 @@ static int upload_tasks(cp_strip *s, std::vector<std::vector<GatherTask>> &lists
 
 static uint32_t list_blocks(const std::vector<GatherTask> &l) {
     uint32_t n = 0;
-    for (auto &t : l) n += task_blocks(t);
+    for (auto &t : l) n += task_blocks(t, kGatherItems);
     return n;
 }
 
@@ -161,9 +184,11 @@ extern "C" int cp_create_strip(int lattice, int L, const uint32_t *primes, int n
         for (auto &p : s->last_dev[b]) p = s->tasks_dev + reinterpret_cast<size_t>(p);
     }
     // e_0: rank 0 of the NCNNN space, polynomial 1
-    CP_CUDA_TRY(cudaMemsetAsync(s->vec[0], 0, ts.S_max * row_words * 4, s->stream));
     std::vector<uint32_t> one(s->P, 1u);
-    CP_CUDA_TRY(cudaMemcpyAsync(s->vec[0], one.data(), 4 * s->P, cudaMemcpyHostToDevice, s->stream));
+    if ((rc = dev_alloc((void **)&s->ones_dev, 4 * s->P))) return rc;
+    CP_CUDA_TRY(cudaMemcpy(s->ones_dev, one.data(), 4 * s->P, cudaMemcpyHostToDevice));
+    CP_CUDA_TRY(cudaMemsetAsync(s->vec[0], 0, ts.S_max * row_words * 4, s->stream));
+    CP_CUDA_TRY(cudaMemcpyAsync(s->vec[0], s->ones_dev, 4 * s->P, cudaMemcpyDeviceToDevice, s->stream));
     CP_CUDA_TRY(cudaStreamSynchronize(s->stream));
     s->cur = 0;
     s->height = 1;
@@ -178,7 +203,7 @@ extern "C" int cp_advance_rows(cp_strip *s, int n_rows) {
         const int b = s->cur;
         for (int i = 0; i < s->L; ++i) {
             int rc = launch_gather(s->row_dev[b][i], (int)s->row_tasks[b][i].size(), list_blocks(s->row_tasks[b][i]),
-                                   s->stream);
+                                   kGatherItems, s->stream);
             if (rc) return rc;
         }
         s->cur = (b + s->L) & 1;
@@ -191,7 +216,7 @@ static int readout(cp_strip *s) {
     const int b = s->cur;
     for (size_t i = 0; i < s->last_tasks[b].size(); ++i) {
         int rc = launch_gather(s->last_dev[b][i], (int)s->last_tasks[b][i].size(),
-                               list_blocks(s->last_tasks[b][i]), s->stream);
+                               list_blocks(s->last_tasks[b][i]), kGatherItems, s->stream);
         if (rc) return rc;
     }
     return launch_transpose_row(s->last_result[b], s->row_out, s->D1, s->P, s->stream);
@@ -225,6 +250,16 @@ extern "C" int cp_strip_info(const cp_strip *s, uint64_t n_states[2], int *degre
     }
     if (degree) *degree = s->D1 - 1;
     if (height) *height = s->height;
+    return CP_OK;
+}
+
+extern "C" int cp_strip_reset(cp_strip *s) {
+    if (!s) return fail(CP_EINVAL, "strip is NULL");
+    const size_t row_words = (size_t)s->D1 * s->P;
+    CP_CUDA_TRY(cudaMemsetAsync(s->vec[0], 0, s->tabs->S_b * row_words * 4, s->stream));
+    CP_CUDA_TRY(cudaMemcpyAsync(s->vec[0], s->ones_dev, 4 * s->P, cudaMemcpyDeviceToDevice, s->stream));
+    s->cur = 0;
+    s->height = 1;
     return CP_OK;
 }
 
