@@ -132,7 +132,10 @@ int cp_select_primes(const uint64_t *draws_host, int n_draws, int n_primes, uint
  */
 typedef struct cp_sweep cp_sweep;
 
-/* tile: gather units per thread (1, 2, 4, 8) or 0 = autotune;
+/* tile: 0 = autotune; 1, 2, 4, 8 = register gather kernel, rows per warp;
+ *       16, 32, 64, 128 = TMA gather kernel, rows per block, optionally plus
+ *       (ring KB << 12) with ring KB in 32..192 (shared-memory ring size) and
+ *       (chunks per consumer thread << 20) with 1, 2 or 4;
  * prime_groups: number of strips per width, dividing n_primes, or 0 = autotune.
  * cuda_stream must be a non-default stream (the program is graph-captured on it).
  * Errors: CP_EINVAL (k < 4, k/2 > CP_MAX_L, series longer than 128 terms, bad

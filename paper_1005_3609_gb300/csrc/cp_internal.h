@@ -39,13 +39,20 @@ struct RankTables {
 };
 
 // A state space of one per-site factor.
+//  SPACE_B: NCNNN partitions in the paper's order (first `size` ranks).
+//  SPACE_X: partitions NCNNN except that e ~ e+1 is allowed (square lattice,
+//           Sec. 3.4).  Ordered by interleaving: the NCNNN partitions in B
+//           order, each NCNNN partition t in which e is alone and e-1 !~ e+1
+//           immediately followed by J_{e,e+1} t.  prefix[b] = number of such t
+//           with B-rank < b, so rank(t) = b + prefix[b] and rank(J t) = that + 1.
 enum SpaceKind : int32_t { SPACE_B = 0, SPACE_X = 1 };
 struct Space {
-    int32_t kind;   // SPACE_B: NCNNN (first `size` ranks); SPACE_X: pair (e, e+1) excepted
+    int32_t kind;
     int32_t m;      // number of sites
     int32_t e;      // excepted pair (SPACE_X)
     int32_t pad;
     uint64_t size;  // number of ranks used
+    const uint32_t *prefix;  // SPACE_X: [M_{m-1} + 1] on the device
 };
 
 // Kind of per-site factor.
@@ -77,12 +84,16 @@ struct TableSet {
     uint64_t S_b = 0, S_max = 0;
     std::vector<SiteTable> row;   // T_1..T_L
     std::vector<SiteTable> last;  // T_1^last..T_{L-1}^last (identity for L = 1)
+    std::vector<uint32_t *> x_prefix;  // square lattice: prefix table of X_e, e = 0..L-2
     size_t bytes = 0;
     ~TableSet();
 };
 
 // Rank tables on the current device (built once per device by a kernel).
 int device_rank_tables(const RankTables **out_dev, RankTables *host_copy);
+
+// Prefix table of the interleaved space X_e on m sites (device, [M_{m-1} + 1]).
+int build_x_prefix(int m, int e, cudaStream_t st, uint32_t **out);
 
 // Build or fetch from the cache the tables of (lattice, L) on the current device.
 int get_tables(int lattice, int L, cudaStream_t stream, std::shared_ptr<TableSet> *out);
@@ -95,25 +106,47 @@ struct GatherTask {
     const uint32_t *row_ptr;
     const uint32_t *edges;
     const uint32_t *primes;   // n_primes words, device
-    uint32_t units;           // n_dst * C  (< 2^31; larger factors are split into several tasks)
-    uint32_t C;               // chunks per row
+    uint32_t rows;            // destination rows of this task
+    uint32_t C;               // chunks per row (16-byte chunks if vec4, else words)
     uint32_t cpd;             // chunks per degree (= n_primes / VEC)
     uint32_t vec4;            // 1: 16-byte chunks, 0: 4-byte chunks
     uint32_t block_begin;     // first block of this task in the launch
-    uint32_t pad[3];
+    uint32_t magic_cpd;       // x / cpd = umulhi(x, magic_cpd) for x * cpd < 2^32 (0: cpd == 1)
+    uint32_t n_primes;
+    uint32_t pad;
 };
 
-constexpr int kGatherThreads = 256;
-constexpr int kGatherItems = 4;  // default (dst, chunk) units per thread
+constexpr int kGatherThreads = 256;  // 8 warps; one warp per destination row at a time
+constexpr int kGatherItems = 4;      // default rows per warp (the tile: 8 * rows per block)
 
-// Append the tasks of one per-site factor (split so that each has < 2^31 units).
+// Append the task of one per-site factor.
 void append_gather_tasks(std::vector<GatherTask> *tasks, const SiteTable &tab, const uint32_t *in,
                          uint32_t *out, const uint32_t *primes_dev, int D1, int P);
+// Gather tile (low 12 bits): 1, 2, 4, 8 = register kernel with that many rows
+// per warp (8 warps per block); 16, 32, 64, 128 = TMA kernel with that many rows
+// per block.  For TMA tiles, bits 12..19 = ring size in KB (0: default) and
+// bits 20..22 = chunks per consumer thread, 1, 2 or 4 (0: 1).  A batch whose
+// rows are not all 16-byte chunked (or too wide for the ring) uses the
+// register kernel.
+constexpr int kTmaRingKbDefault = 48;
+inline int make_tile(int rows, int ring_kb, int passes = 1) { return rows | (ring_kb << 12) | (passes << 20); }
+inline int tile_passes(int tile) { int p = (tile >> 20) & 7; return p ? p : 1; }
+inline int tile_ring_kb(int tile) { int r = (tile >> 12) & 0xFF; return r ? r : kTmaRingKbDefault; }
+bool tile_is_tma(int items);
+bool tma_usable(const GatherTask &t);
 // Blocks of one task and of a whole launch (fills block_begin; returns the grid size).
 uint32_t task_blocks(const GatherTask &t, int items);
 uint32_t assign_blocks(std::vector<GatherTask> &tasks, int items);
-// Launch a batch of tasks (tasks_dev = device copy, block_begin assigned) with `items` units per thread.
+// Effective tile for a batch (falls back from TMA to the register kernel when needed).
+int effective_tile(const std::vector<GatherTask> &tasks, int items);
+// Launch a batch of tasks (tasks_dev = device copy, block_begin assigned for `items`).
 int launch_gather(const GatherTask *tasks_dev, int n_tasks, uint32_t total_blocks, int items, cudaStream_t st);
+// Set the kernels' shared-memory attributes (call outside stream capture).
+int prepare_gather_kernels();
+// Device error word set by bounded waits in kernels; check_device_error syncs
+// `st`, returns CP_ETIMEOUT (and clears the word) if it was set.
+int *device_error_flag();
+int check_device_error(cudaStream_t st);
 
 // Extract the e0 row laid out [D1][P] into [P][D1].
 int launch_transpose_row(const uint32_t *row, uint32_t *out, int D1, int P, cudaStream_t st);

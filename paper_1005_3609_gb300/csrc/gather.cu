@@ -7,12 +7,13 @@
 // is a shift of the coefficient index (Sec. 3.1, 3.5).  Rows are laid out
 // [state][degree][prime], so a shift by one degree is a shift by n_primes
 // words and, for n_primes % 4 == 0, every access is an aligned 16-byte load
-// that reads four primes of one degree.  Arithmetic is add/sub mod p on
-// 32-bit words with p < 2^31 (Sec. 3.5); no floating point.
+// that reads four primes of one degree.  The coefficients are exact integers:
+// each term coef * x (|coef| <= 4, x < p < 2^31) is added to a signed 64-bit
+// accumulator and the sum is reduced modulo p once per word (Sec. 3.5).
 //
 // One launch processes a batch of independent tasks (factors of different
-// strips); each block belongs to one task and covers 256 * ITEMS
-// consecutive (dst, chunk) units of it.
+// strips); each block belongs to one task and covers 8 * RPW consecutive
+// destination rows of it, one warp per row at a time.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -22,32 +23,108 @@
 
 namespace cp {
 
-__device__ __forceinline__ uint32_t add_mod(uint32_t a, uint32_t b, uint32_t p) {
-    uint32_t t = a + b - p;    // in (-p, p) as a signed value
-    return min(t, t + p);      // unsigned min picks the representative in [0, p)
-}
-
-__device__ __forceinline__ uint32_t sub_mod(uint32_t a, uint32_t b, uint32_t p) {
-    uint32_t t = a - b;
-    return min(t, t + p);
-}
-
-// acc += coef * x (mod p) for the small coefficients that the factors produce.
-__device__ __forceinline__ uint32_t axpy_mod(uint32_t acc, uint32_t x, int coef, uint32_t p) {
-    if (coef > 0) {
-        for (int k = 0; k < coef; ++k) acc = add_mod(acc, x, p);
-    } else {
-        for (int k = 0; k < -coef; ++k) acc = sub_mod(acc, x, p);
-    }
-    return acc;
+// v mod p for |v| < 2^40: floor(v/p) from a float estimate (off by at most
+// one), then an exact 32-bit correction.
+__device__ __forceinline__ uint32_t reduce_s64(long long v, uint32_t p, float invp) {
+    const int q = __float2int_rd(__ll2float_rn(v) * invp);
+    uint32_t r = (uint32_t)v - (uint32_t)q * p;  // exact value lies in [-p, 2p)
+    r = min(r, r + p);                           // negative -> + p
+    return min(r, r - p);                        // >= p     -> - p
 }
 
 __device__ __forceinline__ int edge_coef(uint32_t e) { return ((int)(e >> 29) << 29) >> 29; }
 __device__ __forceinline__ uint32_t edge_shift(uint32_t e) { return (e >> kSrcBits) & 3u; }
+__device__ __forceinline__ uint32_t fast_div(uint32_t x, uint32_t magic) { return magic ? __umulhi(x, magic) : x; }
 
-template <int ITEMS>
+constexpr int kWarps = kGatherThreads / 32;
+constexpr unsigned kFull = 0xffffffffu;
+
+// acc += coef * in[src][chunk c - shift*cpd], for the edges held one per lane
+// in `my` (edge j in lane j), up to four loads in flight per lane.
+template <bool V4>
+__device__ __forceinline__ void gather_edges(const GatherTask &t, uint32_t my, int n, uint32_t c, uint32_t deg,
+                                             bool active, long long *acc) {
+    for (int e = 0; e < n; e += 4) {
+        uint32_t q[4];
+        uint4 x[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            q[j] = __shfl_sync(kFull, my, min(e + j, 31));
+            const uint32_t sh = edge_shift(q[j]);
+            x[j] = make_uint4(0, 0, 0, 0);
+            if (e + j < n && active && deg >= sh) {
+                const size_t off = (size_t)(q[j] & kSrcMask) * t.C + (c - sh * t.cpd);
+                if (V4) x[j] = __ldg(reinterpret_cast<const uint4 *>(t.in) + off);
+                else x[j].x = __ldg(t.in + off);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long long cf = edge_coef(q[j]);  // absent edges loaded zero
+            acc[0] += (long long)(int)x[j].x * cf;
+            if (V4) {
+                acc[1] += (long long)(int)x[j].y * cf;
+                acc[2] += (long long)(int)x[j].z * cf;
+                acc[3] += (long long)(int)x[j].w * cf;
+            }
+        }
+    }
+}
+
+// One warp per destination row: the row's CSR entries are read once (two
+// row_ptr words, then the edge list one edge per lane) and broadcast with
+// shuffles; the lanes sweep the row's chunks 32 at a time.  The next row's
+// CSR is fetched while the current row is computed.
+template <int RPW, bool V4>
+__device__ __forceinline__ void gather_rows(const GatherTask &t, uint32_t row0, const uint32_t *s_p,
+                                            const float *s_inv) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t row = row0 + warp;
+    uint32_t rp = (row < t.rows && lane < 2) ? __ldg(t.row_ptr + row + lane) : 0;
+    uint32_t e0 = __shfl_sync(kFull, rp, 0), ne = __shfl_sync(kFull, rp, 1) - e0;
+    uint32_t my = (row < t.rows && lane < ne) ? __ldg(t.edges + e0 + lane) : 0;
+#pragma unroll 1
+    for (int k = 0; k < RPW; ++k) {
+        if (row >= t.rows) return;
+        const uint32_t nrow = row + kWarps;
+        uint32_t nrp = (k + 1 < RPW && nrow < t.rows && lane < 2) ? __ldg(t.row_ptr + nrow + lane) : 0;
+#pragma unroll 1
+        for (uint32_t j = 0; j < t.C; j += 32) {
+            const uint32_t c = j + lane;
+            const bool active = c < t.C;
+            const uint32_t deg = fast_div(c, t.magic_cpd);
+            long long acc[4] = {0, 0, 0, 0};
+            gather_edges<V4>(t, my, (int)min(ne, 32u), c, deg, active, acc);
+            for (uint32_t eb = 32; eb < ne; eb += 32) {  // rows with more than 32 edges
+                const uint32_t mb = (eb + lane < ne) ? __ldg(t.edges + e0 + eb + lane) : 0;
+                gather_edges<V4>(t, mb, (int)min(ne - eb, 32u), c, deg, active, acc);
+            }
+            if (active) {
+                const uint32_t pc = (c - deg * t.cpd) * (V4 ? 4 : 1);
+                const size_t o = (size_t)row * t.C + c;
+                if (V4) {
+                    const uint4 r = make_uint4(reduce_s64(acc[0], s_p[pc], s_inv[pc]),
+                                               reduce_s64(acc[1], s_p[pc + 1], s_inv[pc + 1]),
+                                               reduce_s64(acc[2], s_p[pc + 2], s_inv[pc + 2]),
+                                               reduce_s64(acc[3], s_p[pc + 3], s_inv[pc + 3]));
+                    __stcs(reinterpret_cast<uint4 *>(t.out) + o, r);
+                } else {
+                    __stcs(t.out + o, reduce_s64(acc[0], s_p[pc], s_inv[pc]));
+                }
+            }
+        }
+        row = nrow;
+        e0 = __shfl_sync(kFull, nrp, 0);
+        ne = __shfl_sync(kFull, nrp, 1) - e0;
+        my = (row < t.rows && lane < ne) ? __ldg(t.edges + e0 + lane) : 0;
+    }
+}
+
+template <int RPW>
 __global__ void __launch_bounds__(kGatherThreads) gather_kernel(const GatherTask *__restrict__ tasks, int n_tasks) {
-    // task of this block: the last one whose block_begin <= blockIdx.x
+    __shared__ uint32_t s_p[CP_MAX_PRIMES];
+    __shared__ float s_inv[CP_MAX_PRIMES];
+    // task of this block: the last one whose block_begin <= blockIdx.x (block-uniform)
     int lo = 0, hi = n_tasks - 1;
     const uint32_t b = blockIdx.x;
     while (lo < hi) {
@@ -55,50 +132,41 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(const GatherTask
         if (tasks[mid].block_begin <= b) lo = mid; else hi = mid - 1;
     }
     const GatherTask t = tasks[lo];
-    const uint32_t base = (b - t.block_begin) * (uint32_t)(kGatherThreads * ITEMS);
-#pragma unroll 1
-    for (int it = 0; it < ITEMS; ++it) {
-        const uint32_t u = base + it * kGatherThreads + threadIdx.x;
-        if (u >= t.units) return;
-        const uint32_t dst = u / t.C;
-        const uint32_t c = u - dst * t.C;
-        const uint32_t deg = c / t.cpd;
-        const uint32_t pc = c - deg * t.cpd;
-        const uint32_t e0 = __ldg(t.row_ptr + dst), e1 = __ldg(t.row_ptr + dst + 1);
-        if (t.vec4) {
-            const uint4 pr = __ldg(reinterpret_cast<const uint4 *>(t.primes) + pc);
-            const uint4 *in = reinterpret_cast<const uint4 *>(t.in);
-            uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-            for (uint32_t e = e0; e < e1; ++e) {
-                const uint32_t ed = __ldg(t.edges + e);
-                const uint32_t sh = edge_shift(ed);
-                if (deg < sh) continue;
-                const int cf = edge_coef(ed);
-                const uint4 x = __ldg(in + (size_t)(ed & kSrcMask) * t.C + (c - sh * t.cpd));
-                a0 = axpy_mod(a0, x.x, cf, pr.x);
-                a1 = axpy_mod(a1, x.y, cf, pr.y);
-                a2 = axpy_mod(a2, x.z, cf, pr.z);
-                a3 = axpy_mod(a3, x.w, cf, pr.w);
-            }
-            reinterpret_cast<uint4 *>(t.out)[(size_t)dst * t.C + c] = make_uint4(a0, a1, a2, a3);
-        } else {
-            const uint32_t p = __ldg(t.primes + pc);
-            uint32_t a = 0;
-            for (uint32_t e = e0; e < e1; ++e) {
-                const uint32_t ed = __ldg(t.edges + e);
-                const uint32_t sh = edge_shift(ed);
-                if (deg < sh) continue;
-                const uint32_t x = __ldg(t.in + (size_t)(ed & kSrcMask) * t.C + (c - sh * t.cpd));
-                a = axpy_mod(a, x, edge_coef(ed), p);
-            }
-            t.out[(size_t)dst * t.C + c] = a;
-        }
+    if (threadIdx.x < t.n_primes) {
+        const uint32_t p = __ldg(t.primes + threadIdx.x);
+        s_p[threadIdx.x] = p;
+        s_inv[threadIdx.x] = 1.0f / (float)p;
     }
+    __syncthreads();
+    // rows of the block: row0 + warp + 8 k, k < RPW
+    const uint32_t row0 = (b - t.block_begin) * (uint32_t)(kWarps * RPW);
+    if (t.vec4) gather_rows<RPW, true>(t, row0, s_p, s_inv);
+    else gather_rows<RPW, false>(t, row0, s_p, s_inv);
 }
 
+bool tile_is_tma(int items) { return (items & 0xFFF) >= 16; }
+
 uint32_t task_blocks(const GatherTask &t, int items) {
-    const uint32_t per = (uint32_t)(kGatherThreads * items);
-    return (t.units + per - 1) / per;
+    const uint32_t per = tile_is_tma(items) ? (uint32_t)(items & 0xFFE) : (uint32_t)(kWarps * items);
+    return (t.rows + per - 1) / per;
+}
+
+// For TMA tiles the requested chunks per thread (bits 20..21: 0 = 1) are raised
+// to what the widest row of the batch needs (C <= 256 * passes), and the ring
+// size defaults; a batch the TMA kernel cannot take uses the register kernel.
+int effective_tile(const std::vector<GatherTask> &tasks, int items) {
+    if (!tile_is_tma(items)) return items & 0xFFF;
+    int passes = tile_passes(items);
+    uint32_t max_rb = 0;
+    for (auto &t : tasks) {
+        if (!tma_usable(t)) return kGatherItems;
+        while ((uint32_t)passes * 256u < t.C) passes *= 2;
+        max_rb = std::max(max_rb, t.C * 16u);
+    }
+    int ring = (items >> 12) & 0xFF;
+    if (!ring) ring = kTmaRingKbDefault;
+    ring = std::min(192, std::max(ring, (int)((8u * max_rb + 1023u) / 1024u)));  // >= 8 rows: one per group
+    return make_tile(items & 0xFFF, ring, passes);
 }
 
 uint32_t assign_blocks(std::vector<GatherTask> &tasks, int items) {
@@ -110,39 +178,78 @@ uint32_t assign_blocks(std::vector<GatherTask> &tasks, int items) {
     return blk;
 }
 
+// ceil(2^32 / d) for d >= 2 (0 encodes d == 1).
+static uint32_t magic_for(uint32_t d) { return d <= 1 ? 0u : (uint32_t)(((1ull << 32) + d - 1) / d); }
+
 void append_gather_tasks(std::vector<GatherTask> *tasks, const SiteTable &tab, const uint32_t *in, uint32_t *out,
                          const uint32_t *primes_dev, int D1, int P) {
     const bool v4 = (P % 4) == 0;
     const uint32_t vec = v4 ? 4 : 1;
-    const uint32_t C = (uint32_t)((uint64_t)D1 * P / vec);
-    const uint32_t row_words = (uint32_t)D1 * P;
-    const uint64_t max_rows = std::max<uint64_t>(1, (1ull << 31) / C);
-    for (uint64_t r0 = 0; r0 < tab.n_dst; r0 += max_rows) {
-        uint64_t nr = std::min<uint64_t>(max_rows, tab.n_dst - r0);
-        GatherTask t{};
-        t.in = in;
-        t.out = out + r0 * row_words;
-        t.row_ptr = tab.row_ptr + r0;
-        t.edges = tab.edges;
-        t.primes = primes_dev;
-        t.units = (uint32_t)(nr * C);
-        t.C = C;
-        t.cpd = (uint32_t)P / vec;
-        t.vec4 = v4 ? 1 : 0;
-        tasks->push_back(t);
-    }
+    GatherTask t{};
+    t.in = in;
+    t.out = out;
+    t.row_ptr = tab.row_ptr;
+    t.edges = tab.edges;
+    t.primes = primes_dev;
+    t.rows = (uint32_t)tab.n_dst;
+    t.C = (uint32_t)((uint64_t)D1 * P / vec);
+    t.cpd = (uint32_t)P / vec;
+    t.vec4 = v4 ? 1 : 0;
+    t.magic_cpd = magic_for(t.cpd);
+    t.n_primes = (uint32_t)P;
+    tasks->push_back(t);
 }
+
+int launch_gather_tma(const GatherTask *tasks_dev, int n_tasks, uint32_t total_blocks, int rpb, int *err,
+                      cudaStream_t st, int passes, int ring_kb);
+int prepare_gather_tma();
 
 int launch_gather(const GatherTask *tasks_dev, int n_tasks, uint32_t total_blocks, int items, cudaStream_t st) {
     if (n_tasks <= 0 || total_blocks == 0) return CP_OK;
-    switch (items) {
+    if (tile_is_tma(items))
+        return launch_gather_tma(tasks_dev, n_tasks, total_blocks, items & 0xFFE, device_error_flag(), st,
+                                 tile_passes(items), tile_ring_kb(items));
+    switch (items & 0xFFF) {
         case 1: gather_kernel<1><<<total_blocks, kGatherThreads, 0, st>>>(tasks_dev, n_tasks); break;
         case 2: gather_kernel<2><<<total_blocks, kGatherThreads, 0, st>>>(tasks_dev, n_tasks); break;
         case 4: gather_kernel<4><<<total_blocks, kGatherThreads, 0, st>>>(tasks_dev, n_tasks); break;
         case 8: gather_kernel<8><<<total_blocks, kGatherThreads, 0, st>>>(tasks_dev, n_tasks); break;
-        default: return fail(CP_EINVAL, "gather tile must be 1, 2, 4 or 8");
+        default: return fail(CP_EINVAL, "gather tile must be 1, 2, 4, 8, 16, 32, 64 or 128");
     }
     CP_CUDA_TRY(cudaGetLastError());
+    return CP_OK;
+}
+
+int prepare_gather_kernels() {
+    int rc = prepare_gather_tma();
+    if (rc) return rc;
+    return device_error_flag() ? CP_OK : CP_ECUDA;
+}
+
+int *device_error_flag() {
+    static int *flags[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!flags[dev]) {
+        int *p = nullptr;
+        if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+        cudaMemset(p, 0, sizeof(int));
+        cudaDeviceSynchronize();
+        flags[dev] = p;
+    }
+    return flags[dev];
+}
+
+int check_device_error(cudaStream_t st) {
+    int *f = device_error_flag();
+    if (!f) return fail(CP_ECUDA, "device error word unavailable");
+    CP_CUDA_TRY(cudaStreamSynchronize(st));
+    int h = 0;
+    CP_CUDA_TRY(cudaMemcpy(&h, f, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        CP_CUDA_TRY(cudaMemset(f, 0, sizeof(int)));
+        return fail(CP_ETIMEOUT, "a bounded wait in the TMA gather kernel ran out (flags " + std::to_string(h) + ")");
+    }
     return CP_OK;
 }
 

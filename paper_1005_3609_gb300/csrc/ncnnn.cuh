@@ -141,28 +141,35 @@ __device__ __forceinline__ void ncnnn_unrank(uint64_t r, int lo, int hi, Labels 
     }
 }
 
-// Rank in a space: SPACE_B = NCNNN; SPACE_X = NCNNN first, then the
-// partitions with e ~ e+1 by the rank of their contraction (Sec. 3.4).
+// Rank in a space (SPACE_B: the paper's order; SPACE_X: the interleaved order,
+// see Space).  Returns ~0ull for a partition outside the space's rule.
 __device__ __forceinline__ uint64_t space_rank(const Labels &s, const Space &sp, const RankTables &T) {
-    int m = sp.m;
-    if (sp.kind == SPACE_X && s.v[sp.e] == s.v[sp.e + 1]) {
-        Labels c;
-        for (int i = 0; i <= sp.e; ++i) c.v[i] = s.v[i];
-        for (int i = sp.e + 2; i < m; ++i) c.v[i - 1] = s.v[i];
-        uint64_t r = ncnnn_rank(c, 0, m - 1, T);
-        return r == ~0ull ? r : T.cnt[m] + r;
+    const int m = sp.m;
+    if (sp.kind == SPACE_X) {
+        const int e = sp.e;
+        if (s.v[e] == s.v[e + 1]) {
+            Labels t = s;
+            detach_site(t, m, e);
+            uint64_t b = ncnnn_rank(t, 0, m, T);
+            return b == ~0ull ? b : b + sp.prefix[b] + 1;
+        }
+        uint64_t b = ncnnn_rank(s, 0, m, T);
+        return b == ~0ull ? b : b + sp.prefix[b];
     }
     return ncnnn_rank(s, 0, m, T);
 }
 
 __device__ __forceinline__ void space_unrank(uint64_t r, const Space &sp, Labels &s, const RankTables &T) {
-    int m = sp.m;
-    if (sp.kind == SPACE_X && r >= T.cnt[m]) {
-        Labels c;
-        ncnnn_unrank(r - T.cnt[m], 0, m - 1, c, T);
-        for (int i = 0; i <= sp.e; ++i) s.v[i] = c.v[i];
-        s.v[sp.e + 1] = c.v[sp.e];
-        for (int i = sp.e + 2; i < m; ++i) s.v[i] = c.v[i - 1];
+    const int m = sp.m;
+    if (sp.kind == SPACE_X) {
+        // largest b with b + prefix[b] <= r (strictly increasing in b)
+        uint64_t lo = 0, hi = T.cnt[m] - 1;
+        while (lo < hi) {
+            uint64_t mid = (lo + hi + 1) >> 1;
+            if (mid + sp.prefix[mid] <= r) lo = mid; else hi = mid - 1;
+        }
+        ncnnn_unrank(lo, 0, m, s, T);
+        if (r != lo + sp.prefix[lo]) join_blocks(s, m, sp.e, sp.e + 1);
         return;
     }
     ncnnn_unrank(r, 0, m, s, T);

@@ -88,7 +88,7 @@ struct cp_strip {
     uint32_t *row_out = nullptr;  // [P][D1]
     uint32_t *ones_dev = nullptr;  // P ones (the e_0 row)
     GatherTask *tasks_dev = nullptr;
-    int tasks_cap = 0;
+    int tile = kGatherItems;  // gather tile of this strip's launches
     // precomputed launches: row factors from vec[0] / vec[1], read-out chain
     std::vector<std::vector<GatherTask>> row_tasks[2];
     std::vector<std::vector<GatherTask>> last_tasks[2];
@@ -110,16 +110,16 @@ struct cp_strip {
 static int upload_tasks(cp_strip *s, std::vector<std::vector<GatherTask>> &lists, std::vector<GatherTask *> &ptrs,
                         std::vector<GatherTask> &all) {
     for (auto &l : lists) {
-        assign_blocks(l, kGatherItems);
+        assign_blocks(l, s->tile);
         ptrs.push_back(reinterpret_cast<GatherTask *>(all.size()));  // offset, fixed up later
         all.insert(all.end(), l.begin(), l.end());
     }
     return CP_OK;
 }
 
-static uint32_t list_blocks(const std::vector<GatherTask> &l) {
+static uint32_t list_blocks(const std::vector<GatherTask> &l, int tile) {
     uint32_t n = 0;
-    for (auto &t : l) n += task_blocks(t, kGatherItems);
+    for (auto &t : l) n += task_blocks(t, tile);
     return n;
 }
 
@@ -142,6 +142,7 @@ extern "C" int cp_create_strip(int lattice, int L, const uint32_t *primes, int n
     s->D1 = (int)D + 1;
     s->max_rows = max_rows;
     s->stream = (cudaStream_t)cuda_stream;
+    if ((rc = prepare_gather_kernels())) return rc;
     if ((rc = get_tables(lattice, L, s->stream, &s->tabs))) return rc;
     const TableSet &ts = *s->tabs;
     const size_t row_words = (size_t)s->D1 * s->P;
@@ -154,6 +155,12 @@ extern "C" int cp_create_strip(int lattice, int L, const uint32_t *primes, int n
     if ((rc = dev_alloc((void **)&s->scratch[0], sA * row_words * 4))) return rc;
     if ((rc = dev_alloc((void **)&s->scratch[1], sB * row_words * 4))) return rc;
     if ((rc = dev_alloc((void **)&s->row_out, row_words * 4))) return rc;
+    // TMA gather when the rows are 16-byte chunked and fit the ring, else the register kernel
+    {
+        std::vector<GatherTask> probe;
+        append_gather_tasks(&probe, ts.row[0], s->vec[0], s->vec[1], s->primes_dev, s->D1, s->P);
+        s->tile = effective_tile(probe, 64);
+    }
     // launches of one row (starting from vec[b]) and of the read-out chain from vec[b]
     std::vector<GatherTask> all;
     for (int b = 0; b < 2; ++b) {
@@ -202,8 +209,8 @@ extern "C" int cp_advance_rows(cp_strip *s, int n_rows) {
     for (int r = 0; r < n_rows; ++r) {
         const int b = s->cur;
         for (int i = 0; i < s->L; ++i) {
-            int rc = launch_gather(s->row_dev[b][i], (int)s->row_tasks[b][i].size(), list_blocks(s->row_tasks[b][i]),
-                                   kGatherItems, s->stream);
+            int rc = launch_gather(s->row_dev[b][i], (int)s->row_tasks[b][i].size(),
+                                   list_blocks(s->row_tasks[b][i], s->tile), s->tile, s->stream);
             if (rc) return rc;
         }
         s->cur = (b + s->L) & 1;
@@ -216,7 +223,7 @@ static int readout(cp_strip *s) {
     const int b = s->cur;
     for (size_t i = 0; i < s->last_tasks[b].size(); ++i) {
         int rc = launch_gather(s->last_dev[b][i], (int)s->last_tasks[b][i].size(),
-                               list_blocks(s->last_tasks[b][i]), kGatherItems, s->stream);
+                               list_blocks(s->last_tasks[b][i], s->tile), s->tile, s->stream);
         if (rc) return rc;
     }
     return launch_transpose_row(s->last_result[b], s->row_out, s->D1, s->P, s->stream);
@@ -237,7 +244,7 @@ extern "C" int cp_read_coeffs(cp_strip *s, uint32_t *out, size_t out_len, int *h
     int rc = readout(s);
     if (rc) return rc;
     CP_CUDA_TRY(cudaMemcpyAsync(out, s->row_out, 4ull * s->P * s->D1, cudaMemcpyDeviceToHost, s->stream));
-    CP_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if ((rc = check_device_error(s->stream))) return rc;
     if (height_out) *height_out = s->height;
     return CP_OK;
 }

@@ -58,6 +58,7 @@ struct cp_sweep {
     int *err_dev = nullptr;
     GatherTask *tasks_dev = nullptr;
     std::vector<uint32_t> step_off, step_ntasks, step_blocks;
+    std::vector<int> step_tile;
     uint64_t updates = 0, bytes = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -94,7 +95,8 @@ static void count_work(cp_sweep *sw, const SiteTable &t, int Pg) {
     sw->bytes += 4ull * (t.n_src + t.n_dst) * sw->D1 * Pg + 4ull * (t.n_dst + 1 + t.nnz);
 }
 
-static int build_program(cp_sweep *sw) {
+// Strips and buffers: one strip per width (and prime group), band rectangles.
+static int build_strips(cp_sweep *sw) {
     const int ngroups = sw->groups, Pg = sw->Pg;
     const size_t row_words = (size_t)sw->D1 * Pg;
     int rc;
@@ -102,7 +104,6 @@ static int build_program(cp_sweep *sw) {
     for (int r = 1; 2 * r <= sw->k; ++r)
         for (int s = r; r + s <= sw->k; ++s)
             if (r + s >= sw->k - 3) sw->rects.push_back(make_int2(r, s));
-    const int n_rects = (int)sw->rects.size();
     for (int g = 0; g < ngroups; ++g) {
         for (int r = 1; 2 * r <= sw->k; ++r) {
             SweepStrip st;
@@ -114,15 +115,39 @@ static int build_program(cp_sweep *sw) {
             if (st.heights.empty()) continue;
             if ((rc = get_tables(sw->lattice, r, sw->stream, &st.tabs))) return rc;
             const TableSet &ts = *st.tabs;
-            for (int b = 0; b < 2; ++b)
-                if ((rc = dev_alloc((void **)&st.vec[b], ts.S_max * row_words * 4))) return rc;
-            uint64_t sA = r >= 2 ? ts.last[0].n_dst : 1, sB = r >= 3 ? ts.last[1].n_dst : 1;
-            if ((rc = dev_alloc((void **)&st.scratch[0], sA * row_words * 4))) return rc;
-            if ((rc = dev_alloc((void **)&st.scratch[1], sB * row_words * 4))) return rc;
             sw->strips.push_back(st);
+            SweepStrip &sp = sw->strips.back();
+            for (int b = 0; b < 2; ++b)
+                if ((rc = dev_alloc((void **)&sp.vec[b], ts.S_max * row_words * 4))) return rc;
+            uint64_t sA = r >= 2 ? ts.last[0].n_dst : 1, sB = r >= 3 ? ts.last[1].n_dst : 1;
+            if ((rc = dev_alloc((void **)&sp.scratch[0], sA * row_words * 4))) return rc;
+            if ((rc = dev_alloc((void **)&sp.scratch[1], sB * row_words * 4))) return rc;
         }
     }
-    // per-step task lists
+    return CP_OK;
+}
+
+static int enqueue_program(cp_sweep *sw);
+
+// Launch program for gather tile `tile`: per-step task lists, block assignment,
+// device task array, and the CUDA graph of the whole sweep.
+static int build_program(cp_sweep *sw, int tile) {
+    const int Pg = sw->Pg;
+    const int n_rects = (int)sw->rects.size();
+    const size_t row_words = (size_t)sw->D1 * Pg;
+    int rc;
+    sw->tile = tile;
+    sw->updates = sw->bytes = 0;
+    sw->step_off.clear();
+    sw->step_ntasks.clear();
+    sw->step_blocks.clear();
+    sw->step_tile.clear();
+    if (sw->exec) cudaGraphExecDestroy(sw->exec);
+    if (sw->graph) cudaGraphDestroy(sw->graph);
+    sw->exec = nullptr;
+    sw->graph = nullptr;
+    dev_free(sw->tasks_dev);
+    sw->tasks_dev = nullptr;
     std::vector<std::vector<GatherTask>> steps;
     auto at = [&](size_t t) -> std::vector<GatherTask> & {
         if (steps.size() <= t) steps.resize(t + 1);
@@ -158,13 +183,27 @@ static int build_program(cp_sweep *sw) {
     }
     std::vector<GatherTask> all;
     for (auto &l : steps) {
+        const int et = effective_tile(l, tile);
         sw->step_off.push_back((uint32_t)all.size());
         sw->step_ntasks.push_back((uint32_t)l.size());
-        sw->step_blocks.push_back(assign_blocks(l, sw->tile));
+        sw->step_tile.push_back(et);
+        sw->step_blocks.push_back(assign_blocks(l, et));
         all.insert(all.end(), l.begin(), l.end());
     }
     if ((rc = dev_alloc((void **)&sw->tasks_dev, std::max<size_t>(1, all.size()) * sizeof(GatherTask)))) return rc;
     CP_CUDA_TRY(cudaMemcpy(sw->tasks_dev, all.data(), all.size() * sizeof(GatherTask), cudaMemcpyHostToDevice));
+    // capture the program into one graph
+    CP_CUDA_TRY(cudaStreamBeginCapture(sw->stream, cudaStreamCaptureModeThreadLocal));
+    rc = enqueue_program(sw);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(sw->stream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(CP_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    sw->graph = g;
+    CP_CUDA_TRY(cudaGraphInstantiate(&sw->exec, g, 0));
     return CP_OK;
 }
 
@@ -176,8 +215,8 @@ static int enqueue_program(cp_sweep *sw) {
         CP_CUDA_TRY(cudaMemcpyAsync(st.vec[0], sw->ones_dev, 4 * sw->Pg, cudaMemcpyDeviceToDevice, sw->stream));
     }
     for (size_t t = 0; t < sw->step_off.size(); ++t) {
-        int rc = launch_gather(sw->tasks_dev + sw->step_off[t], (int)sw->step_ntasks[t], sw->step_blocks[t], sw->tile,
-                               sw->stream);
+        int rc = launch_gather(sw->tasks_dev + sw->step_off[t], (int)sw->step_ntasks[t], sw->step_blocks[t],
+                               sw->step_tile[t], sw->stream);
         if (rc) return rc;
     }
     SeriesParams sp{};
@@ -202,11 +241,11 @@ static int sweep_build(int lattice, int k, const uint32_t *primes, int P, int ti
     sw->P = P;
     sw->n = n_terms_for(lattice, k);
     sw->D1 = sw->n;
-    sw->tile = tile;
     sw->groups = groups;
     sw->Pg = P / groups;
     sw->stream = stream;
     int rc;
+    if ((rc = prepare_gather_kernels())) return rc;
     if ((rc = dev_alloc((void **)&sw->primes_dev, 4 * CP_MAX_PRIMES))) return rc;
     CP_CUDA_TRY(cudaMemcpy(sw->primes_dev, primes, 4 * P, cudaMemcpyHostToDevice));
     std::vector<uint32_t> ones(CP_MAX_PRIMES, 1u);
@@ -220,21 +259,10 @@ static int sweep_build(int lattice, int k, const uint32_t *primes, int P, int ti
     if ((rc = dev_alloc((void **)&sw->series_dev, 4ull * 3 * P * sw->n))) return rc;
     if ((rc = dev_alloc((void **)&sw->err_dev, sizeof(int)))) return rc;
     CP_CUDA_TRY(cudaMemset(sw->err_dev, 0, sizeof(int)));
-    if ((rc = build_program(sw.get()))) return rc;
+    if ((rc = build_strips(sw.get()))) return rc;
     if ((rc = dev_alloc((void **)&sw->rects_dev, sizeof(int2) * n_rects))) return rc;
     CP_CUDA_TRY(cudaMemcpy(sw->rects_dev, sw->rects.data(), sizeof(int2) * n_rects, cudaMemcpyHostToDevice));
-    // capture the program into one graph
-    CP_CUDA_TRY(cudaStreamBeginCapture(sw->stream, cudaStreamCaptureModeThreadLocal));
-    rc = enqueue_program(sw.get());
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamEndCapture(sw->stream, &g);
-    if (rc) {
-        if (g) cudaGraphDestroy(g);
-        return rc;
-    }
-    if (e != cudaSuccess) return fail(CP_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-    sw->graph = g;
-    CP_CUDA_TRY(cudaGraphInstantiate(&sw->exec, g, 0));
+    if ((rc = build_program(sw.get(), tile))) return rc;
     *out = sw.release();
     return CP_OK;
 }
@@ -268,7 +296,15 @@ extern "C" int cp_sweep_create(int lattice, int k, const uint32_t *primes, int n
     int rc = check_primes(primes, n_primes);
     if (rc) return rc;
     if (!cuda_stream) return fail(CP_EINVAL, "the sweep needs a non-default stream (graph capture)");
-    if (tile != 0 && tile != 1 && tile != 2 && tile != 4 && tile != 8) return fail(CP_EINVAL, "tile must be 0, 1, 2, 4 or 8");
+    {
+        const int rows = tile & 0xFFF, ring = (tile >> 12) & 0xFF, passes = (tile >> 20) & 7;
+        const bool reg = (rows == 1 || rows == 2 || rows == 4 || rows == 8) && (tile >> 12) == 0;
+        const bool tma = (rows == 16 || rows == 32 || rows == 64 || rows == 128) && (tile >> 23) == 0 &&
+                         (ring == 0 || (ring >= 32 && ring <= 192)) && (passes <= 2 || passes == 4);
+        if (tile != 0 && !reg && !tma)
+            return fail(CP_EINVAL, "tile must be 0 (autotune), 1, 2, 4, 8 (register kernel) or 16, 32, 64, 128 "
+                                   "(TMA) + (ring KB 32..192 << 12) + (chunks per thread 1, 2, 4 << 20)");
+    }
     if (prime_groups < 0 || (prime_groups > 0 && n_primes % prime_groups != 0))
         return fail(CP_EINVAL, "prime_groups must divide n_primes");
     cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -283,30 +319,37 @@ extern "C" int cp_sweep_create(int lattice, int k, const uint32_t *primes, int n
             return sweep_build(lattice, k, primes, n_primes, tile ? tile : it->second.first,
                                prime_groups ? prime_groups : it->second.second, st, out);
     }
-    // autotune: time each candidate once (after a warm-up run) and keep the fastest
-    std::vector<int> tiles = tile ? std::vector<int>{tile} : std::vector<int>{1, 2, 4, 8};
+    // autotune: for each prime grouping build the strips once, re-tile the
+    // launch program for each candidate tile, time one graph run (after a
+    // warm-up run) and keep the fastest (tile, grouping)
+    std::vector<int> tiles = tile ? std::vector<int>{tile}
+                                  : std::vector<int>{make_tile(64, 48, 1), make_tile(32, 48, 1),
+                                                     make_tile(128, 48, 1), make_tile(64, 40, 1), 4};
     std::vector<int> grps;
     if (prime_groups) grps = {prime_groups};
     else
-        for (int g : {1, 2, 4})
+        for (int g : {1, 2})
             if (n_primes % g == 0 && (n_primes / g) % 4 == 0) grps.push_back(g);
     if (grps.empty()) grps = {1};
     float best = 1e30f;
     int bt = tiles[0], bg = grps[0];
-    for (int g : grps)
-        for (int t : tiles) {
-            cp_sweep *cand = nullptr;
-            if ((rc = sweep_build(lattice, k, primes, n_primes, t, g, st, &cand))) return rc;
+    for (int g : grps) {
+        cp_sweep *cand = nullptr;
+        if ((rc = sweep_build(lattice, k, primes, n_primes, tiles[0], g, st, &cand))) return rc;
+        for (size_t ti = 0; ti < tiles.size(); ++ti) {
+            if (ti > 0 && (rc = build_program(cand, tiles[ti]))) break;
             float ms = 0;
-            rc = sweep_time_once(cand, &ms);
-            delete cand;
-            if (rc) return rc;
+            if ((rc = sweep_time_once(cand, &ms))) break;
+            if ((rc = check_device_error(st))) break;
             if (ms < best) {
                 best = ms;
-                bt = t;
+                bt = tiles[ti];
                 bg = g;
             }
         }
+        delete cand;
+        if (rc) return rc;
+    }
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tuned[key] = {bt, bg};
@@ -323,6 +366,8 @@ extern "C" int cp_sweep_run(cp_sweep *sw) {
 extern "C" int cp_sweep_sync(cp_sweep *sw) {
     if (!sw) return fail(CP_EINVAL, "sweep is NULL");
     CP_CUDA_TRY(cudaStreamSynchronize(sw->stream));
+    int rc = check_device_error(sw->stream);
+    if (rc) return rc;
     int herr = 0;
     CP_CUDA_TRY(cudaMemcpy(&herr, sw->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
     if (herr) return fail(CP_ESTATE, "a rectangle's P~ lacks constant term 1");
@@ -408,8 +453,8 @@ extern "C" int cp_sweep_profile(cp_sweep *sw, float *gather_ms, int *n_gather, f
     }
     for (size_t t = 0; t < nst && rc == CP_OK; ++t) {
         cudaEventRecord(ev[2 * t], sw->stream);
-        rc = launch_gather(sw->tasks_dev + sw->step_off[t], (int)sw->step_ntasks[t], sw->step_blocks[t], sw->tile,
-                           sw->stream);
+        rc = launch_gather(sw->tasks_dev + sw->step_off[t], (int)sw->step_ntasks[t], sw->step_blocks[t],
+                           sw->step_tile[t], sw->stream);
         cudaEventRecord(ev[2 * t + 1], sw->stream);
     }
     CP_CUDA_TRY(cudaEventRecord(ev[2 * nst + 1], sw->stream));

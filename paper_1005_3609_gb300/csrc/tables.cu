@@ -274,6 +274,21 @@ __global__ void sort_segments_kernel(const uint32_t *row_ptr, uint64_t n_dst, ui
     }
 }
 
+// flag[b] = 1 if the NCNNN partition of rank b has e alone and e-1 !~ e+1, so that
+// J_{e,e+1} of it lies in X_e (every partition of X_e with e ~ e+1 arises once).
+__global__ void x_partner_kernel(int m, int e, const RankTables *Tg, uint32_t *flag) {
+    __shared__ RankTables T;
+    stage_tables(T, Tg);
+    uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= T.cnt[m]) return;
+    Labels s;
+    ncnnn_unrank(b, 0, m, s, T);
+    bool alone = true;
+    for (int i = 0; i < m; ++i)
+        if (i != e && s.v[i] == s.v[e]) alone = false;
+    flag[b] = (alone && (e == 0 || s.v[e - 1] != s.v[e + 1])) ? 1u : 0u;
+}
+
 // ------------------------------------------------------------------ host side
 
 static int scan_exclusive(const uint32_t *cnt, uint64_t n, uint32_t *row_ptr, cudaStream_t st) {
@@ -289,6 +304,41 @@ static int scan_exclusive(const uint32_t *cnt, uint64_t n, uint32_t *row_ptr, cu
     cudaStreamSynchronize(st);
     dev_free(sums);
     if (e != cudaSuccess) return fail(CP_ECUDA, std::string("scan: ") + cudaGetErrorString(e));
+    return CP_OK;
+}
+
+int build_x_prefix(int m, int e, cudaStream_t st, uint32_t **out) {
+    const RankTables *T_dev = nullptr;
+    RankTables T;
+    int rc = device_rank_tables(&T_dev, &T);
+    if (rc) return rc;
+    const uint64_t Sb = T.cnt[m];
+    uint32_t *flag = nullptr, *pre = nullptr;
+    if ((rc = dev_alloc((void **)&flag, Sb * 4))) return rc;
+    if ((rc = dev_alloc((void **)&pre, (Sb + 1) * 4))) {
+        dev_free(flag);
+        return rc;
+    }
+    x_partner_kernel<<<(unsigned)((Sb + 127) / 128), 128, 0, st>>>(m, e, T_dev, flag);
+    cudaError_t ce = cudaGetLastError();
+    if (ce != cudaSuccess) {
+        dev_free(flag);
+        dev_free(pre);
+        return fail(CP_ECUDA, std::string("x_partner: ") + cudaGetErrorString(ce));
+    }
+    rc = scan_exclusive(flag, Sb, pre, st);
+    dev_free(flag);
+    if (rc) {
+        dev_free(pre);
+        return rc;
+    }
+    uint32_t total = 0;
+    CP_CUDA_TRY(cudaMemcpy(&total, pre + Sb, 4, cudaMemcpyDeviceToHost));
+    if (total != T.cnt[m - 1]) {
+        dev_free(pre);
+        return fail(CP_ESTATE, "excepted space has the wrong size");
+    }
+    *out = pre;
     return CP_OK;
 }
 
@@ -364,6 +414,7 @@ static int build_table(const OpDesc &op, const RankTables *T_dev, cudaStream_t s
 }
 
 TableSet::~TableSet() {
+    for (auto p : x_prefix) dev_free(p);
     for (auto &t : row) {
         dev_free(t.row_ptr);
         dev_free(t.edges);
@@ -379,7 +430,7 @@ static int identity_table(int m, SiteTable *tab) {
     OpDesc op{};
     op.kind = OP_IDENTITY;
     op.m = m;
-    op.in = Space{SPACE_B, m, 0, 0, 1};
+    op.in = Space{SPACE_B, m, 0, 0, 1, nullptr};
     op.out = op.in;
     tab->op = op;
     tab->n_src = tab->n_dst = tab->nnz = 1;
@@ -405,6 +456,14 @@ static int build_tableset(int lattice, int L, cudaStream_t st, std::shared_ptr<T
     const uint64_t Sx = L >= 2 ? T.cnt[L] + T.cnt[L - 1] : Sb;
     ts->S_b = Sb;
     ts->S_max = lattice == CP_SQUARE ? Sx : Sb;
+    if (lattice == CP_SQUARE) {
+        for (int e = 0; e + 1 < L; ++e) {
+            uint32_t *pre = nullptr;
+            if ((rc = build_x_prefix(L, e, st, &pre))) return rc;
+            ts->x_prefix.push_back(pre);
+            ts->bytes += (Sb + 1) * 4;
+        }
+    }
     for (int i = 0; i < L; ++i) {
         OpDesc op{};
         op.m = L;
@@ -412,12 +471,12 @@ static int build_tableset(int lattice, int L, cudaStream_t st, std::shared_ptr<T
         if (lattice == CP_SQUARE) {
             op.kind = OP_SQUARE;
             op.max_terms = 4;
-            op.in = i == 0 ? Space{SPACE_B, L, 0, 0, Sb} : Space{SPACE_X, L, i - 1, 0, Sx};
-            op.out = i == L - 1 ? Space{SPACE_B, L, 0, 0, Sb} : Space{SPACE_X, L, i, 0, Sx};
+            op.in = i == 0 ? Space{SPACE_B, L, 0, 0, Sb, nullptr} : Space{SPACE_X, L, i - 1, 0, Sx, ts->x_prefix[i - 1]};
+            op.out = i == L - 1 ? Space{SPACE_B, L, 0, 0, Sb, nullptr} : Space{SPACE_X, L, i, 0, Sx, ts->x_prefix[i]};
         } else {
             op.kind = OP_TRIANGULAR;
             op.max_terms = 8;
-            op.in = Space{SPACE_B, L, 0, 0, Sb};
+            op.in = Space{SPACE_B, L, 0, 0, Sb, nullptr};
             op.out = op.in;
         }
         SiteTable tab;
@@ -436,8 +495,8 @@ static int build_tableset(int lattice, int L, cudaStream_t st, std::shared_ptr<T
             op.m = L;
             op.i = i;
             op.max_terms = 2;
-            op.in = Space{SPACE_B, L, 0, 0, T.cnt[L - i]};
-            op.out = Space{SPACE_B, L, 0, 0, T.cnt[L - i - 1]};
+            op.in = Space{SPACE_B, L, 0, 0, T.cnt[L - i], nullptr};
+            op.out = Space{SPACE_B, L, 0, 0, T.cnt[L - i - 1], nullptr};
             SiteTable tab;
             if ((rc = build_table(op, T_dev, st, &tab))) return rc;
             ts->bytes += (tab.n_dst + 1 + tab.nnz) * 4;
@@ -519,15 +578,22 @@ int check_space(int kind, int m, int e, uint64_t *n_bad, uint64_t *size) {
     RankTables T;
     int rc = device_rank_tables(&T_dev, &T);
     if (rc) return rc;
-    Space sp{kind, m, e, 0, kind == SPACE_X ? T.cnt[m] + T.cnt[m - 1] : T.cnt[m]};
+    Space sp{kind, m, e, 0, kind == SPACE_X ? T.cnt[m] + T.cnt[m - 1] : T.cnt[m], nullptr};
+    uint32_t *pre = nullptr;
+    if (kind == SPACE_X && (rc = build_x_prefix(m, e, 0, &pre))) return rc;
+    sp.prefix = pre;
     unsigned long long *bad = nullptr;
-    if ((rc = dev_alloc((void **)&bad, 8))) return rc;
+    if ((rc = dev_alloc((void **)&bad, 8))) {
+        dev_free(pre);
+        return rc;
+    }
     CP_CUDA_TRY(cudaMemset(bad, 0, 8));
     check_space_kernel<<<(unsigned)((sp.size + 127) / 128), 128>>>(sp, T_dev, bad);
     CP_CUDA_TRY(cudaGetLastError());
     unsigned long long h = 0;
     CP_CUDA_TRY(cudaMemcpy(&h, bad, 8, cudaMemcpyDeviceToHost));
     dev_free(bad);
+    dev_free(pre);
     *n_bad = h;
     *size = sp.size;
     return CP_OK;
@@ -549,15 +615,22 @@ int enumerate_space(int kind, int m, int e, uint8_t *out_host, uint64_t max_stat
     RankTables T;
     int rc = device_rank_tables(&T_dev, &T);
     if (rc) return rc;
-    Space sp{kind, m, e, 0, kind == SPACE_X ? T.cnt[m] + T.cnt[m - 1] : T.cnt[m]};
+    Space sp{kind, m, e, 0, kind == SPACE_X ? T.cnt[m] + T.cnt[m - 1] : T.cnt[m], nullptr};
     *size = sp.size;
     if (sp.size > max_states) return fail(CP_EINVAL, "output buffer too small");
+    uint32_t *pre = nullptr;
+    if (kind == SPACE_X && (rc = build_x_prefix(m, e, 0, &pre))) return rc;
+    sp.prefix = pre;
     uint8_t *d = nullptr;
-    if ((rc = dev_alloc((void **)&d, sp.size * m))) return rc;
+    if ((rc = dev_alloc((void **)&d, sp.size * m))) {
+        dev_free(pre);
+        return rc;
+    }
     enumerate_kernel<<<(unsigned)((sp.size + 127) / 128), 128>>>(sp, T_dev, d);
     CP_CUDA_TRY(cudaGetLastError());
     CP_CUDA_TRY(cudaMemcpy(out_host, d, sp.size * m, cudaMemcpyDeviceToHost));
     dev_free(d);
+    dev_free(pre);
     return CP_OK;
 }
 

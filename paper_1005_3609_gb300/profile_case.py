@@ -24,7 +24,7 @@ def main():
     import synthetic_inputs
     import paper_1005_3609_gb300 as cp
     primes = cp.select_primes(synthetic_inputs.prime_draws(0, 64), a.primes)
-    with cp.Strip(a.lattice, a.L, primes, max_degree=a.D, max_rows=a.rows + 1) as s:
+    with cp.Strip(a.lattice, a.L, primes, max_degree=a.D, max_rows=a.rows + 2) as s:
         s.advance(1)  # warm-up row
         s.advance(a.rows)
         s.read()

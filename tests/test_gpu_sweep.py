@@ -58,12 +58,16 @@ def test_small_sweep_matches_oracle(stream, lattice, k, n_primes):
             assert res[x].tolist() == gpu_util.residues_of(series[x], primes), x
 
 
-def test_tile_and_group_choices_agree(stream):
+@pytest.mark.parametrize("k", [16, 17])
+def test_tile_and_group_choices_agree(stream, k):
+    # k = 16: rows of 29 degrees (chunk counts that do not divide 256);
+    # k = 17: rows of 32 degrees, so 16/8/4 primes give 128/64/32 chunks and the
+    # TMA kernel runs 2, 4 and 8 consumer row groups
     primes = gpu_util.seed_primes(16, seed=2)
     ref = None
-    for tile in (1, 2, 4, 8):
+    for tile in (1, 2, 4, 8, 16, 32, 64, 128):
         for groups in (1, 2, 4):
-            with cp.Sweep("square", 16, primes, stream, tile=tile, prime_groups=groups) as sw:
+            with cp.Sweep("square", k, primes, stream, tile=tile, prime_groups=groups) as sw:
                 sw.run()
                 sw.sync()
                 got = (sw.read_series().tobytes(), {k: v.tobytes() for k, v in sw.read_ptilde().items()})
