@@ -111,6 +111,28 @@ int cp_crt_device(const uint32_t *residues_dev, const uint32_t *primes_host, int
                   int n_coeffs, uint32_t *limbs_dev, int limbs_per_coeff, void *cuda_stream);
 
 /*
+ * cp_crt_static -- cp_crt without any device allocation.  The paper has no
+ * counterpart: this is a service of the library.  cp_crt allocates device
+ * buffers on every call; callers that cannot allocate device memory (their
+ * device memory is entirely owned by another allocator, or their service
+ * forbids new allocations once it runs) use this entry point instead.  Same
+ * arguments, result and errors as cp_crt.  The residues and limbs are staged in
+ * one fixed device array of CP_CRT_STATIC_BYTES bytes (residues rounded up to
+ * 256 bytes, then limbs); a call needing more returns CP_EINVAL with the sizes
+ * in cp_last_error().  The array is created when the library is loaded, once
+ * per device, and held until the process exits.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Synchronous (legacy
+ * default stream).  All calls share the array and it keeps the last call's
+ * contents (every limb is rewritten, nothing needs clearing), so calls that
+ * overlap on the GPU -- from several host threads at once -- race; serialise
+ * them.
+ */
+#define CP_CRT_STATIC_BYTES (8u << 20)
+int cp_crt_static(const uint32_t *residues_host, const uint32_t *primes_host, int n_primes,
+                  int n_coeffs, uint32_t *limbs_host, int limbs_per_coeff);
+
+/*
  * cp_select_primes -- the prime set (Sec. 3.5 leaves the choice open): each
  * draw in [2^30, 2^31) is mapped on the GPU to the smallest prime >= draw
  * (deterministic Miller-Rabin, bases 2, 7, 61); repeats and results >= 2^31

@@ -56,6 +56,7 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_float)]),
     "cp_crt": (ctypes.c_int, [u32p, u32p, ctypes.c_int, ctypes.c_int, u32p, ctypes.c_int]),
     "cp_crt_device": (ctypes.c_int, [vp, u32p, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp]),
+    "cp_crt_static": (ctypes.c_int, [u32p, u32p, ctypes.c_int, ctypes.c_int, u32p, ctypes.c_int]),
     "cp_select_primes": (ctypes.c_int, [u64p, ctypes.c_int, ctypes.c_int, u32p]),
     "cp_clear_table_cache": (None, []),
     "cp_last_error": (ctypes.c_char_p, []),
@@ -126,6 +127,18 @@ def crt(residues, primes, limbs_per_coeff=None):
         limbs_per_coeff = (31 * P + 2 + 31) // 32 + 1
     out = np.zeros((n, limbs_per_coeff), dtype=np.uint32)
     check("cp_crt", load().cp_crt(rp, pp, P, n, out.ctypes.data_as(u32p), limbs_per_coeff))
+    return limbs_to_ints(out)
+
+
+def crt_static(residues, primes, limbs_per_coeff=None):
+    """As crt(), through cp_crt_static (no device allocation; fixed-size staging array)."""
+    res, rp = _u32(residues)
+    pr, pp = _u32(primes)
+    P, n = res.shape
+    if limbs_per_coeff is None:
+        limbs_per_coeff = (31 * P + 2 + 31) // 32 + 1
+    out = np.zeros((n, limbs_per_coeff), dtype=np.uint32)
+    check("cp_crt_static", load().cp_crt_static(rp, pp, P, n, out.ctypes.data_as(u32p), limbs_per_coeff))
     return limbs_to_ints(out)
 
 

@@ -5,6 +5,7 @@
 // representative in (-prod/2, prod/2] as two's complement.
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -248,4 +249,68 @@ extern "C" int cp_debug_enumerate_space(int kind, int m, int e, uint8_t *out_hos
     if (m < 1 || m > CP_MAX_L || (kind != 0 && kind != 1) || (kind == 1 && (e < 0 || e + 1 >= m)))
         return fail(CP_EINVAL, "bad space");
     return enumerate_space(kind, m, e, out_host, max_states, size);
+}
+
+// ------------------------------------------------------------------ CRT without allocation
+//
+// cp_crt allocates two device buffers on every call.  Some callers cannot do
+// that: a process whose device memory is entirely handed to another allocator
+// (a framework's caching allocator, a fixed arena reserved at start-up), or a
+// service that forbids new device allocations once it is serving.
+// cp_crt_static runs the same kernel with its residues and limbs staged in
+// this fixed device array instead.  The array exists once per device that
+// loads the library and is held until the process exits.
+
+static __device__ __align__(256) uint8_t g_crt_scratch[CP_CRT_STATIC_BYTES];
+
+namespace {
+std::mutex g_crt_static_mu;
+uint8_t *g_crt_static_ptr[64];  // device address of g_crt_scratch, per device
+}  // namespace
+
+// Device address of the array on the current device, looked up once per device.
+static int crt_static_scratch(uint8_t **out) {
+    int dev = 0;
+    CP_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CP_EINVAL, "device index");
+    std::lock_guard<std::mutex> lk(g_crt_static_mu);
+    if (!g_crt_static_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_crt_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(CP_ECUDA, std::string("cudaGetSymbolAddress(g_crt_scratch): ") + cudaGetErrorString(e));
+        g_crt_static_ptr[dev] = (uint8_t *)p;
+    }
+    *out = g_crt_static_ptr[dev];
+    return CP_OK;
+}
+
+extern "C" int cp_crt_static(const uint32_t *res, const uint32_t *primes, int P, int n_coeffs, uint32_t *limbs_out,
+                             int limbs) {
+    CrtParams prm{};
+    int rc = crt_params(primes, P, n_coeffs, limbs, &prm);
+    if (rc) return rc;
+    if (n_coeffs == 0) return CP_OK;
+    if (!res || !limbs_out) return fail(CP_EINVAL, "NULL argument");
+    const size_t res_bytes = 4ull * P * n_coeffs;
+    const size_t res_span = (res_bytes + 255) & ~(size_t)255;
+    const size_t limb_bytes = 4ull * limbs * n_coeffs;
+    if (res_span + limb_bytes > CP_CRT_STATIC_BYTES)
+        return fail(CP_EINVAL, "cp_crt_static: residues (" + std::to_string(res_bytes) + " bytes) plus limbs (" +
+                                   std::to_string(limb_bytes) + " bytes) exceed CP_CRT_STATIC_BYTES (" +
+                                   std::to_string((size_t)CP_CRT_STATIC_BYTES) + ")");
+    uint8_t *base = nullptr;
+    if ((rc = crt_static_scratch(&base))) return rc;
+    uint32_t *r_d = reinterpret_cast<uint32_t *>(base);
+    uint32_t *l_d = reinterpret_cast<uint32_t *>(base + res_span);
+    // the kernel reads only the residues copied here and writes every limb, so no
+    // part of the array has to be cleared between calls
+    cudaError_t e = cudaMemcpy(r_d, res, res_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        crt_kernel<<<(n_coeffs + 63) / 64, 64>>>(r_d, l_d, prm);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(limbs_out, l_d, limb_bytes, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(CP_ECUDA, std::string("cp_crt_static: ") + cudaGetErrorString(e));
+    return CP_OK;
 }
