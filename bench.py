@@ -172,9 +172,16 @@ def load_traffic(kernel_key):
 def gather_source_sha():
     import hashlib
     h = hashlib.sha256()
-    for f in ("gather.cu", "cp_internal.h"):
+    for f in ("gather.cu", "gather_tma.cu", "cp_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_1005_3609_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
+
+
+def tile_name(tile):
+    rows, ring, passes = tile & 0xFFF, (tile >> 12) & 0xFF, (tile >> 20) & 7
+    if rows <= 8:
+        return "register gather kernel, %d rows/warp" % rows
+    return "TMA gather kernel, %d rows/block, %d KB ring, %d chunk(s)/thread" % (rows, ring or 48, passes or 1)
 
 
 def plain_run(cp, torch, lattice, k, primes, stream):
@@ -233,8 +240,11 @@ def gpu_arm(args):
     torch.cuda.set_device(local)
     cp.load()
     lattice, k, P = args.lattice, args.k, args.primes
-    draws = synthetic_inputs.prime_draws(rank, 256)
-    primes = cp.select_primes(draws, P)
+    # one prime stream, each rank its own slice of P primes (no overlap between ranks)
+    from paper_1005_3609_gb300 import distributed as shard
+    all_primes = cp.select_primes(synthetic_inputs.prime_draws(0, 64 * world + 64), P * world)
+    lo, hi = shard.rank_prime_slice(P * world, world, rank)
+    primes = all_primes[lo:hi]
     stream = torch.cuda.Stream()
     t_setup = time.perf_counter()
     sw = cp.Sweep(lattice, k, primes, stream, tile=args.tile, prime_groups=args.groups)
@@ -323,6 +333,11 @@ def gpu_arm(args):
     from paper_1005_3609_gb300._lib import limbs_to_ints
     import numpy as np
     series = [limbs_to_ints(pinned_out.numpy().view(np.uint32).reshape(3, n, limbs)[x]) for x in range(3)]
+    if dist:  # the one exchange: rank 0 gathers every rank's residues and recombines all primes
+        got = shard.gather_residues(sw.read_series(), primes, dist)
+        if rank == 0:
+            res_all, primes_all = got
+            series = [cp.crt(res_all[x], primes_all) for x in range(3)]
 
     # ---- roofline of the dominant kernel (batched gather), one ungraphed pass with per-launch events
     gather_ms, n_gather, pass_ms = sw.profile()
@@ -336,7 +351,7 @@ def gpu_arm(args):
                 "algorithmic_bytes_per_launch": sw.bytes_per_run / n_gather,
                 "avg_launch_ms": gather_ms / n_gather,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peak else "fallback 6800 GB/s",
-                "kernel": "gather_kernel<%d> (batched per-site gather)" % sw.tile}
+                "kernel": "batched per-site gather: %s" % tile_name(sw.tile)}
     if not peak:
         roofline["peak"] = 6800.0
         roofline["frac"] = round(achieved / 6800.0, 4)
@@ -350,12 +365,13 @@ def gpu_arm(args):
                "config": {"workload": "%s lattice finite-lattice sweep k=%d: %d rectangles r x s (r<=s, %d<=r+s<=%d, "
                                       "widths 1..%d), %d primes/GPU (seed=rank), P~ to w^%d" %
                                       (lattice, k, sw.n_rects, k - 3, k, k // 2, P, n - 1),
-                          "parallelism": "weak: each rank sweeps its own %d primes, no collective" % P if world > 1
+                          "parallelism": ("weak: each rank sweeps its own %d primes, no collective while timed; "
+                                          "rank 0 gathers the series residues afterwards" % P) if world > 1
                           else "single GPU",
                           "l2": "no flush: working set > L2 (width-16 vectors %.2f GB each)" %
                                 (strip_bytes_max(lattice, k, n, P) / 1e9),
                           "tables": "built once per (lattice, width) before timing (%.2f s incl. autotune)" % setup_s,
-                          "tile": sw.tile, "prime_groups": sw.prime_groups,
+                          "tile": tile_name(sw.tile), "prime_groups": sw.prime_groups,
                           "updates_per_step": sw.updates_per_run, "algorithmic_bytes_per_step": sw.bytes_per_run},
                "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
