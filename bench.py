@@ -429,6 +429,110 @@ def strip_bytes_max(lattice, k, n, P):
     return S * n * P * 4
 
 
+# ---------------------------------------------------------------- serving workload
+
+def serve_stream(cp, sv, reqs, primes_of, rate_scale=1.0):
+    """Feed requests at their (scaled) Poisson arrival times in real time; step the
+    server whenever it has work.  Returns per-request (queue s, service s, total s) and wall s."""
+    t0 = time.perf_counter()
+    ids, i = [], 0
+    n = len(reqs)
+    done = set()
+    while len(done) < n:
+        now = time.perf_counter() - t0
+        while i < n and reqs[i]["arrival_s"] / rate_scale <= now:
+            r = reqs[i]
+            ids.append(sv.submit(r["lattice"], r["L"], r["N"], primes_of(r)))
+            i += 1
+        if len(ids) > len(done):
+            _, _, fin = sv.step()
+            if fin:
+                done.update(sv.poll())
+        elif i < n:
+            time.sleep(max(0.0, min(0.01, reqs[i]["arrival_s"] / rate_scale - now)))
+    wall = time.perf_counter() - t0
+    lat = []
+    for rid in ids:
+        _, _, (ts, ta, td) = sv.result(rid)
+        lat.append((ta - ts, td - ta, td - ts))
+    return lat, wall
+
+
+def pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(round(q / 100.0 * (len(xs) - 1))))]
+
+
+def serve_arm(args):
+    import torch
+    import paper_1005_3609_gb300 as cp
+    torch.cuda.set_device(0)
+    cp.load()
+    reqs = synthetic_inputs.serving_requests(seed=1, rate_per_s=200.0, n=10000)[: args.serve_n]
+    pcache = {}
+
+    def primes_of(r):
+        key = (r["prime_seed"], r["n_primes"])
+        if key not in pcache:
+            pcache[key] = cp.select_primes(synthetic_inputs.prime_draws(r["prime_seed"] % (2 ** 31), 64),
+                                           r["n_primes"])
+        return pcache[key]
+
+    for r in reqs:
+        primes_of(r)
+    stream = torch.cuda.Stream()
+    budget = int(args.serve_budget_gb * (1 << 30))
+    with cp.Server(budget, max_active=args.serve_max_active, stream=stream) as sv:
+        # warm-up: tables of every (lattice, width) in the stream, one tiny request each
+        for lat in ("square", "triangular"):
+            for L in sorted({r["L"] for r in reqs}):
+                rid = sv.submit(lat, L, 1, [primes_of(reqs[0])[0]])
+                while sv.result(rid)[0] != sv.DONE:
+                    sv.step()
+                sv.release(rid)
+        sv.poll()
+        st0 = sv.stats()
+        clocks = ClockSampler(0)
+        clocks.start()
+        lat, wall = serve_stream(cp, sv, reqs, primes_of)
+        clk = clocks.stop()
+        st1 = sv.stats()
+        upd = st1["updates"] - st0["updates"]
+        cap_rps = len(reqs) / wall
+        # supplementary stream at 0.7x the measured capacity (added; arrival times rescaled)
+        scale = 0.7 * cap_rps / 200.0
+        lat07, wall07 = serve_stream(cp, sv, reqs, primes_of, rate_scale=scale)
+    # plain: the same requests one (rectangle, prime) at a time
+    t = time.perf_counter()
+    upd_plain = 0
+    for r in reqs:
+        for p in primes_of(r):
+            with cp.Strip(r["lattice"], r["L"], [p], max_degree=-1, max_rows=r["N"], stream=stream) as s:
+                s.advance(r["N"] - 1)
+                s.read()
+    plain_s = time.perf_counter() - t
+    out = {"metric": "served rectangle solves: state-coeff updates/s and p50/p99 latency", "value": upd / wall,
+           "unit": "updates/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": wall * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+           "config": {"workload": "serving: Poisson stream seed 1, 200 req/s offered, first %d of 10000 requests; "
+                                  "lattice U{square, triangular}, L U{4..16}, N in {L, L+1}, 4..16 primes, full degree"
+                                  % len(reqs),
+                      "mem_budget_gb": args.serve_budget_gb, "max_active": args.serve_max_active},
+           "requests_per_s": cap_rps,
+           "server_steps": st1["steps"] - st0["steps"], "gpu_launches": st1["launches"] - st0["launches"],
+           "latency_s": {"p50": pct([x[2] for x in lat], 50), "p99": pct([x[2] for x in lat], 99),
+                         "queue_p50": pct([x[0] for x in lat], 50), "queue_p99": pct([x[0] for x in lat], 99),
+                         "service_p50": pct([x[1] for x in lat], 50), "service_p99": pct([x[1] for x in lat], 99)},
+           "at_0.7x_capacity (added)": {"offered_req_per_s": 200.0 * scale, "wall_s": wall07,
+                                        "p50": pct([x[2] for x in lat07], 50), "p99": pct([x[2] for x in lat07], 99),
+                                        "queue_p99": pct([x[0] for x in lat07], 99)},
+           "served_vs_plain": {"served_s": wall, "plain_s": plain_s, "speedup": plain_s / wall,
+                               "plain": "each request one prime at a time, 1-prime strip, per-site launches"}}
+    if clk:
+        out["clocks"] = clk
+    print(json.dumps(out))
+
+
 # ---------------------------------------------------------------- reference arm (the CPU oracle)
 
 def reference_arm(args):
@@ -478,10 +582,16 @@ def main():
     ap.add_argument("--cpu-widths", type=int, default=13, help="widths of the CPU-baseline sample")
     ap.add_argument("--ref-widths", type=int, default=11, help="widths of each reference-arm step")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "serve"])
+    ap.add_argument("--serve-n", type=int, default=300, help="requests of the serving stream to run")
+    ap.add_argument("--serve-budget-gb", type=float, default=150.0)
+    ap.add_argument("--serve-max-active", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "serve":
+        serve_arm(args)
     else:
         gpu_arm(args)
 

@@ -157,7 +157,7 @@ typedef struct cp_sweep cp_sweep;
 /* tile: 0 = autotune; 1, 2, 4, 8 = register gather kernel, rows per warp;
  *       16, 32, 64, 128 = TMA gather kernel, rows per block, optionally plus
  *       (ring KB << 12) with ring KB in 32..192 (shared-memory ring size) and
- *       (chunks per consumer thread << 20) with 1, 2 or 4;
+ *       (chunks per consumer thread << 20) with 1, 2, 4 or 8;
  * prime_groups: number of strips per width, dividing n_primes, or 0 = autotune.
  * cuda_stream must be a non-default stream (the program is graph-captured on it).
  * Errors: CP_EINVAL (k < 4, k/2 > CP_MAX_L, series longer than 128 terms, bad
@@ -203,6 +203,50 @@ int cp_sweep_set_primes(cp_sweep *sw, const uint32_t *primes_host, int n_primes)
 int cp_sweep_profile(cp_sweep *sw, float *gather_ms, int *n_gather, float *total_ms);
 
 void cp_sweep_destroy(cp_sweep *sw);
+
+/* ---------------------------------------------------------------- serving
+ * Rectangle solves of mixed lattice / L / N / primes with continuous batching.
+ * Each request is solved at full degree D = L*N - 1 (Sec. 3, eq. (Z_from_T)).
+ * At admission, queued requests for the same rectangle (lattice, L, N) are
+ * merged into one job: one strip whose rows carry all their primes (padded to
+ * a multiple of four).  The server owns one device arena of mem_budget_bytes
+ * (allocated at creation) from which every admitted job takes its vectors;
+ * admission is by footprint (first fit, queue order; a job that does not fit
+ * yet does not block smaller ones), at most max_active jobs at once.  Each
+ * step advances every active job by one per-site factor in one batched launch.
+ */
+typedef struct cp_server cp_server;
+
+int cp_server_create(size_t mem_budget_bytes, int max_active, void *cuda_stream, cp_server **out);
+
+/* Queue a solve; *req_id identifies it.  CP_ENOMEM if its footprint exceeds
+ * the whole budget (it could never be admitted), CP_EINVAL on bad arguments. */
+int cp_server_submit(cp_server *sv, int lattice, int L, int N, const uint32_t *primes_host, int n_primes,
+                     uint64_t *req_id);
+
+/* One step: admit queued requests that fit; one batched launch (two if some
+ * rows are not 16-byte chunked) of the next per-site factor of every active
+ * request (row factors, then its read-out chain); copy out and retire the
+ * finished ones, returning their memory.  Synchronises the stream. */
+int cp_server_step(cp_server *sv, int *n_active, int *n_queued, int *n_finished);
+
+/* State of a request (0 queued, 1 active, 2 done, -1 failed) and, when done,
+ * its residues out_host[n_primes][L*N]; times_s = {submitted, admitted,
+ * finished} on the host's monotonic clock (seconds). */
+int cp_server_result(cp_server *sv, uint64_t req_id, uint32_t *out_host, size_t out_len, int *state,
+                     double times_s[3]);
+
+/* Ids of requests finished since the last poll (up to max_ids, oldest first). */
+int cp_server_poll(cp_server *sv, uint64_t *ids_out, int max_ids, int *n_ids);
+
+/* Forget a finished request (its result is dropped). */
+int cp_server_release(cp_server *sv, uint64_t req_id);
+
+/* Steps run, gather launches, updates (output words), free arena bytes. */
+int cp_server_stats(const cp_server *sv, uint64_t *steps, uint64_t *launches, uint64_t *updates,
+                    size_t *arena_free_bytes);
+
+void cp_server_destroy(cp_server *sv);
 
 /* Release the per-device cache of transfer-matrix tables (not in use by a
  * live strip). */

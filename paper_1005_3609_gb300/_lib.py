@@ -54,6 +54,16 @@ SIGNATURES = {
     "cp_sweep_set_primes": (ctypes.c_int, [vp, u32p, ctypes.c_int]),
     "cp_sweep_profile": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_float)]),
+    "cp_server_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, vp, ctypes.POINTER(vp)]),
+    "cp_server_submit": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, u32p, ctypes.c_int, u64p]),
+    "cp_server_step": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(ctypes.c_int)]),
+    "cp_server_result": (ctypes.c_int, [vp, ctypes.c_uint64, u32p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_double)]),
+    "cp_server_release": (ctypes.c_int, [vp, ctypes.c_uint64]),
+    "cp_server_poll": (ctypes.c_int, [vp, u64p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "cp_server_stats": (ctypes.c_int, [vp, u64p, u64p, u64p, ctypes.POINTER(ctypes.c_size_t)]),
+    "cp_server_destroy": (None, [vp]),
     "cp_crt": (ctypes.c_int, [u32p, u32p, ctypes.c_int, ctypes.c_int, u32p, ctypes.c_int]),
     "cp_crt_device": (ctypes.c_int, [vp, u32p, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp]),
     "cp_crt_static": (ctypes.c_int, [u32p, u32p, ctypes.c_int, ctypes.c_int, u32p, ctypes.c_int]),
@@ -280,6 +290,76 @@ class Sweep:
     def close(self):
         if self._h:
             load().cp_sweep_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Server:
+    """Continuous-batching server of rectangle solves (cp_server_*)."""
+
+    QUEUED, ACTIVE, DONE, FAILED = 0, 1, 2, -1
+
+    def __init__(self, mem_budget_bytes, max_active=64, stream=None):
+        h = vp()
+        check("cp_server_create", load().cp_server_create(int(mem_budget_bytes), int(max_active),
+                                                          vp(_stream_handle(stream)), ctypes.byref(h)))
+        self._h = h
+        self.shapes = {}
+
+    def submit(self, lattice, L, N, primes):
+        pr, pp = _u32(primes)
+        rid = ctypes.c_uint64()
+        check("cp_server_submit", load().cp_server_submit(self._h, lattice_id(lattice), L, N, pp, len(pr),
+                                                          ctypes.byref(rid)))
+        self.shapes[rid.value] = (len(pr), L * N)
+        return rid.value
+
+    def step(self):
+        a, q, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check("cp_server_step", load().cp_server_step(self._h, ctypes.byref(a), ctypes.byref(q), ctypes.byref(f)))
+        return a.value, q.value, f.value
+
+    def result(self, rid):
+        """(state, residues [P][L*N] or None, (t_submit, t_admit, t_done))"""
+        P, n = self.shapes[rid]
+        out = np.zeros((P, n), dtype=np.uint32)
+        st = ctypes.c_int()
+        ts = (ctypes.c_double * 3)()
+        check("cp_server_result", load().cp_server_result(self._h, rid, out.ctypes.data_as(u32p), out.size,
+                                                          ctypes.byref(st), ts))
+        return st.value, (out if st.value == self.DONE else None), tuple(ts)
+
+    def poll(self, max_ids=4096):
+        """Ids finished since the last poll."""
+        buf = (ctypes.c_uint64 * max_ids)()
+        n = ctypes.c_int()
+        check("cp_server_poll", load().cp_server_poll(self._h, buf, max_ids, ctypes.byref(n)))
+        return [int(buf[k]) for k in range(n.value)]
+
+    def release(self, rid):
+        check("cp_server_release", load().cp_server_release(self._h, rid))
+        self.shapes.pop(rid, None)
+
+    def stats(self):
+        s, l, u, f = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_size_t()
+        check("cp_server_stats", load().cp_server_stats(self._h, ctypes.byref(s), ctypes.byref(l), ctypes.byref(u),
+                                                        ctypes.byref(f)))
+        return {"steps": s.value, "launches": l.value, "updates": u.value, "arena_free_bytes": f.value}
+
+    def close(self):
+        if self._h:
+            load().cp_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -113,24 +113,27 @@ struct GatherTask {
     uint32_t block_begin;     // first block of this task in the launch
     uint32_t magic_cpd;       // x / cpd = umulhi(x, magic_cpd) for x * cpd < 2^32 (0: cpd == 1)
     uint32_t n_primes;
-    uint32_t pad;
+    uint32_t c0;              // first chunk of the rows handled by this task
+    uint32_t cw;              // chunks handled (a column range [c0, c0 + cw) of every row)
+    uint32_t pad[3];
 };
 
 constexpr int kGatherThreads = 256;  // 8 warps; one warp per destination row at a time
 constexpr int kGatherItems = 4;      // default rows per warp (the tile: 8 * rows per block)
 
-// Append the task of one per-site factor.
+// Append the task(s) of one per-site factor: rows of 16-byte chunks wider than
+// 256 chunks are split into column tasks of at most 256 chunks each.
 void append_gather_tasks(std::vector<GatherTask> *tasks, const SiteTable &tab, const uint32_t *in,
                          uint32_t *out, const uint32_t *primes_dev, int D1, int P);
 // Gather tile (low 12 bits): 1, 2, 4, 8 = register kernel with that many rows
 // per warp (8 warps per block); 16, 32, 64, 128 = TMA kernel with that many rows
 // per block.  For TMA tiles, bits 12..19 = ring size in KB (0: default) and
-// bits 20..22 = chunks per consumer thread, 1, 2 or 4 (0: 1).  A batch whose
+// bits 20..23 = chunks per consumer thread, 1, 2, 4 or 8 (0: 1).  A batch whose
 // rows are not all 16-byte chunked (or too wide for the ring) uses the
 // register kernel.
 constexpr int kTmaRingKbDefault = 48;
 inline int make_tile(int rows, int ring_kb, int passes = 1) { return rows | (ring_kb << 12) | (passes << 20); }
-inline int tile_passes(int tile) { int p = (tile >> 20) & 7; return p ? p : 1; }
+inline int tile_passes(int tile) { int p = (tile >> 20) & 15; return p ? p : 1; }
 inline int tile_ring_kb(int tile) { int r = (tile >> 12) & 0xFF; return r ? r : kTmaRingKbDefault; }
 bool tile_is_tma(int items);
 bool tma_usable(const GatherTask &t);

@@ -89,9 +89,9 @@ __device__ __forceinline__ void gather_rows(const GatherTask &t, uint32_t row0, 
         const uint32_t nrow = row + kWarps;
         uint32_t nrp = (k + 1 < RPW && nrow < t.rows && lane < 2) ? __ldg(t.row_ptr + nrow + lane) : 0;
 #pragma unroll 1
-        for (uint32_t j = 0; j < t.C; j += 32) {
+        for (uint32_t j = t.c0; j < t.c0 + t.cw; j += 32) {
             const uint32_t c = j + lane;
-            const bool active = c < t.C;
+            const bool active = c < t.c0 + t.cw;
             const uint32_t deg = fast_div(c, t.magic_cpd);
             long long acc[4] = {0, 0, 0, 0};
             gather_edges<V4>(t, my, (int)min(ne, 32u), c, deg, active, acc);
@@ -160,8 +160,8 @@ int effective_tile(const std::vector<GatherTask> &tasks, int items) {
     uint32_t max_rb = 0;
     for (auto &t : tasks) {
         if (!tma_usable(t)) return kGatherItems;
-        while ((uint32_t)passes * 256u < t.C) passes *= 2;
-        max_rb = std::max(max_rb, t.C * 16u);
+        while ((uint32_t)passes * 256u < t.cw) passes *= 2;
+        max_rb = std::max(max_rb, t.cw * 16u);
     }
     int ring = (items >> 12) & 0xFF;
     if (!ring) ring = kTmaRingKbDefault;
@@ -197,7 +197,12 @@ void append_gather_tasks(std::vector<GatherTask> *tasks, const SiteTable &tab, c
     t.vec4 = v4 ? 1 : 0;
     t.magic_cpd = magic_for(t.cpd);
     t.n_primes = (uint32_t)P;
-    tasks->push_back(t);
+    const uint32_t ncol = v4 ? (t.C + 255) / 256 : 1;
+    for (uint32_t k = 0; k < ncol; ++k) {  // balanced column ranges
+        t.c0 = (uint32_t)((uint64_t)t.C * k / ncol);
+        t.cw = (uint32_t)((uint64_t)t.C * (k + 1) / ncol) - t.c0;
+        tasks->push_back(t);
+    }
 }
 
 int launch_gather_tma(const GatherTask *tasks_dev, int n_tasks, uint32_t total_blocks, int rpb, int *err,

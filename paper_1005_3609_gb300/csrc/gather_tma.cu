@@ -28,7 +28,7 @@ namespace cp {
 constexpr int kTmaConsumers = 8;                      // consumer warps
 constexpr int kTmaThreads = 32 * (kTmaConsumers + 1);  // + producer warp
 constexpr int kTmaMaxSlots = 96;
-constexpr int kTmaMaxPasses = 4;                       // C <= 4 * 256 chunks
+constexpr int kTmaMaxPasses = 8;                       // C <= 8 * 256 chunks
 constexpr long long kWaitCycles = 1ll << 31;           // ~1 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -83,7 +83,7 @@ __device__ __forceinline__ uint32_t reduce_s64_t(long long v, uint32_t p, float 
 // waits on).  More chunks per thread spread the per-edge work (barrier wait,
 // edge decode, release) over more data and put G rows in flight per block.
 template <int RPB, int PASSES>
-__global__ void __launch_bounds__(kTmaThreads, PASSES == 1 ? 4 : (PASSES == 2 ? 3 : 2))
+__global__ void __launch_bounds__(kTmaThreads, PASSES == 1 ? 4 : (PASSES == 2 ? 3 : (PASSES == 4 ? 2 : 1)))
     gather_tma_kernel(const GatherTask *__restrict__ tasks, int n_tasks, uint32_t ring_bytes, int *err) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ uint64_t full_bar[kTmaMaxSlots], empty_bar[kTmaMaxSlots];
@@ -107,11 +107,13 @@ __global__ void __launch_bounds__(kTmaThreads, PASSES == 1 ? 4 : (PASSES == 2 ? 
     const GatherTask t = tasks[lo];
     const uint32_t row0 = (b - t.block_begin) * (uint32_t)RPB;
     const uint32_t nrows = min((uint32_t)RPB, t.rows - row0);
-    const uint32_t RB = t.C * 16u;    // bytes per row
-    const uint32_t DB = t.cpd * 16u;  // bytes per degree
-    const uint32_t D1 = t.C / t.cpd;
+    // a slot holds the column range [c0, c0 + cw) of a row: slot chunk x is
+    // source chunk c0 + x - shift * cpd (absent where that is negative)
+    const uint32_t RB = t.cw * 16u;                             // slot bytes
+    const uint8_t *in_bytes = reinterpret_cast<const uint8_t *>(t.in);
+    const size_t src_row_bytes = (size_t)t.C * 16u;
     uint32_t G = 1;
-    while (G < 8 && (t.C * 2 * G + 255) / 256 <= (uint32_t)PASSES) G *= 2;
+    while (G < 8 && (t.cw * 2 * G + 255) / 256 <= (uint32_t)PASSES) G *= 2;
     // G sub-rings of nsub slots each; slot of sub-ring position x = x mod nsub, phase = (x / nsub) & 1
     uint32_t nsub = min((uint32_t)kTmaMaxSlots / G, ring_bytes / (G * RB));
     if (nsub == 0) {  // ring smaller than one row per group: refuse (block-uniform)
@@ -175,13 +177,15 @@ __global__ void __launch_bounds__(kTmaThreads, PASSES == 1 ? 4 : (PASSES == 2 ? 
                     }
                     if (ok) {
                         meta[s] = qj;
-                        const uint32_t sh = (qj >> kSrcBits) & 3u;
-                        const uint32_t bytes = sh < D1 ? (D1 - sh) * DB : 0u;
+                        const uint32_t back = ((qj >> kSrcBits) & 3u) * t.cpd;  // shift in chunks
+                        const uint32_t skip = back > t.c0 ? min(back - t.c0, t.cw) : 0u;
+                        const uint32_t bytes = (t.cw - skip) * 16u;
                         const uint32_t fb = smem_addr(&full_bar[s]);
                         if (bytes) {
                             mbar_arrive_expect_tx(fb, bytes);
-                            bulk_copy_g2s(smem_addr(smem + (size_t)s * RB + sh * DB),
-                                          reinterpret_cast<const uint8_t *>(t.in) + (size_t)(qj & kSrcMask) * RB,
+                            bulk_copy_g2s(smem_addr(smem + (size_t)s * RB + skip * 16u),
+                                          in_bytes + (size_t)(qj & kSrcMask) * src_row_bytes +
+                                              (size_t)(t.c0 + skip - back) * 16u,
                                           bytes, fb);
                         } else {
                             mbar_arrive(fb);
@@ -217,8 +221,8 @@ __global__ void __launch_bounds__(kTmaThreads, PASSES == 1 ? 4 : (PASSES == 2 ? 
     const uint32_t gt = threadIdx.x - 32 - grp * GT;  // thread within the group
     uint32_t deg[PASSES];
 #pragma unroll
-    for (int p = 0; p < PASSES; ++p) deg[p] = fast_div_u(gt + GT * p, t.magic_cpd);
-    const int passes = (int)((t.C + GT - 1) / GT);
+    for (int p = 0; p < PASSES; ++p) deg[p] = fast_div_u(t.c0 + gt + GT * p, t.magic_cpd);
+    const int passes = (int)((t.cw + GT - 1) / GT);
     uint32_t slot = 0, phase = 0;  // next slot of this sub-ring and its phase parity
     for (uint32_t r = grp; r < nrows; r += G) {
         const uint32_t ne = s_rp[r + 1] - s_rp[r];
@@ -237,8 +241,8 @@ __global__ void __launch_bounds__(kTmaThreads, PASSES == 1 ? 4 : (PASSES == 2 ? 
             const uint4 *sd = reinterpret_cast<const uint4 *>(smem + (size_t)s * RB);
 #pragma unroll
             for (int p = 0; p < PASSES; ++p) {
-                const uint32_t c = gt + GT * p;
-                if (p < passes && c < t.C && deg[p] >= sh) {
+                const uint32_t c = gt + GT * p;  // chunk within the column range
+                if (p < passes && c < t.cw && deg[p] >= sh) {
                     const uint4 x = sd[c];
                     acc[p][0] += (long long)(int)x.x * cf;
                     acc[p][1] += (long long)(int)x.y * cf;
@@ -253,12 +257,12 @@ __global__ void __launch_bounds__(kTmaThreads, PASSES == 1 ? 4 : (PASSES == 2 ? 
                 phase ^= 1u;
             }
         }
-        const size_t orow = (size_t)(row0 + r) * t.C;
+        const size_t orow = (size_t)(row0 + r) * t.C + t.c0;
 #pragma unroll
         for (int p = 0; p < PASSES; ++p) {
             const uint32_t c = gt + GT * p;
-            if (p < passes && c < t.C) {
-                const uint32_t pc = (c - deg[p] * t.cpd) * 4;
+            if (p < passes && c < t.cw) {
+                const uint32_t pc = (t.c0 + c - deg[p] * t.cpd) * 4;
                 const uint4 v = make_uint4(reduce_s64_t(acc[p][0], s_p[pc], s_inv[pc]),
                                            reduce_s64_t(acc[p][1], s_p[pc + 1], s_inv[pc + 1]),
                                            reduce_s64_t(acc[p][2], s_p[pc + 2], s_inv[pc + 2]),
@@ -275,8 +279,8 @@ constexpr uint32_t kTmaRingMax = 192 * 1024;
 constexpr uint32_t kTmaRingMin = 32 * 1024;
 
 bool tma_usable(const GatherTask &t) {
-    if (!t.vec4 || t.C > (uint32_t)(256 * kTmaMaxPasses)) return false;
-    return kTmaRingMax / (t.C * 16u) >= 8;
+    if (!t.vec4 || t.cw > (uint32_t)(256 * kTmaMaxPasses)) return false;
+    return kTmaRingMax / (t.cw * 16u) >= 8;
 }
 
 template <int RPB, int PASSES>
@@ -302,7 +306,7 @@ int prepare_gather_tma() {
     if (dev < 0 || dev >= 64) return fail(CP_EINVAL, "device index");
     if (done[dev]) return CP_OK;
     int rc;
-    if ((rc = set_attrs<1>()) || (rc = set_attrs<2>()) || (rc = set_attrs<4>())) return rc;
+    if ((rc = set_attrs<1>()) || (rc = set_attrs<2>()) || (rc = set_attrs<4>()) || (rc = set_attrs<8>())) return rc;
     done[dev] = true;
     return CP_OK;
 }
@@ -318,7 +322,7 @@ static void launch_passes(int rpb, const GatherTask *tasks_dev, int n_tasks, uin
     }
 }
 
-// passes: chunks per consumer thread (1, 2 or 4); every task must have C <= 256 * passes.
+// passes: chunks per consumer thread (1, 2, 4 or 8); every task must have C <= 256 * passes.
 int launch_gather_tma(const GatherTask *tasks_dev, int n_tasks, uint32_t total_blocks, int rpb, int *err,
                       cudaStream_t st, int passes, int ring_kb) {
     if (n_tasks <= 0 || total_blocks == 0) return CP_OK;
@@ -329,7 +333,8 @@ int launch_gather_tma(const GatherTask *tasks_dev, int n_tasks, uint32_t total_b
     if (dyn > kTmaRingMax) dyn = kTmaRingMax;
     if (passes == 1) launch_passes<1>(rpb, tasks_dev, n_tasks, total_blocks, dyn, err, st);
     else if (passes == 2) launch_passes<2>(rpb, tasks_dev, n_tasks, total_blocks, dyn, err, st);
-    else launch_passes<4>(rpb, tasks_dev, n_tasks, total_blocks, dyn, err, st);
+    else if (passes == 4) launch_passes<4>(rpb, tasks_dev, n_tasks, total_blocks, dyn, err, st);
+    else launch_passes<8>(rpb, tasks_dev, n_tasks, total_blocks, dyn, err, st);
     CP_CUDA_TRY(cudaGetLastError());
     return CP_OK;
 }

@@ -297,13 +297,14 @@ extern "C" int cp_sweep_create(int lattice, int k, const uint32_t *primes, int n
     if (rc) return rc;
     if (!cuda_stream) return fail(CP_EINVAL, "the sweep needs a non-default stream (graph capture)");
     {
-        const int rows = tile & 0xFFF, ring = (tile >> 12) & 0xFF, passes = (tile >> 20) & 7;
+        const int rows = tile & 0xFFF, ring = (tile >> 12) & 0xFF, passes = (tile >> 20) & 15;
         const bool reg = (rows == 1 || rows == 2 || rows == 4 || rows == 8) && (tile >> 12) == 0;
-        const bool tma = (rows == 16 || rows == 32 || rows == 64 || rows == 128) && (tile >> 23) == 0 &&
-                         (ring == 0 || (ring >= 32 && ring <= 192)) && (passes <= 2 || passes == 4);
+        const bool tma = (rows == 16 || rows == 32 || rows == 64 || rows == 128) && (tile >> 24) == 0 &&
+                         (ring == 0 || (ring >= 32 && ring <= 192)) &&
+                         (passes <= 2 || passes == 4 || passes == 8);
         if (tile != 0 && !reg && !tma)
             return fail(CP_EINVAL, "tile must be 0 (autotune), 1, 2, 4, 8 (register kernel) or 16, 32, 64, 128 "
-                                   "(TMA) + (ring KB 32..192 << 12) + (chunks per thread 1, 2, 4 << 20)");
+                                   "(TMA) + (ring KB 32..192 << 12) + (chunks per thread 1, 2, 4, 8 << 20)");
     }
     if (prime_groups < 0 || (prime_groups > 0 && n_primes % prime_groups != 0))
         return fail(CP_EINVAL, "prime_groups must divide n_primes");

@@ -196,3 +196,11 @@ def test_select_primes_matches_oracle():
     for seed in (0, 1, 7):
         draws = synthetic_inputs.prime_draws(seed, 128)
         assert cp.select_primes(draws, 24) == ocrt.primes_from_draws(draws, 24)
+
+
+def test_wide_rows_eight_chunk_passes():
+    # 32 primes x 136 coefficients: 1088 chunks of 16 bytes per row (the TMA kernel's 8-pass variant)
+    primes = gpu_util.seed_primes(32, seed=21)
+    want = tm_exact.ptilde("square", 8, 17)
+    got = run_strip("square", 8, 17, primes)
+    assert got.tolist() == gpu_util.residues_of(want, primes)
