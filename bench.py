@@ -380,7 +380,7 @@ def gpu_arm(args):
                "hbm_gbs_algorithmic": sw.bytes_per_run * args.steps / (ms / 1e3) / 1e9}
         if clk:
             out["clocks"] = clk
-        if lattice == "square" and k == 33:
+        if lattice == "square" and k in (33, 41):
             t = table1()
             out["check"] = {"series_match_table1": series[0] == t["alpha"][:n] and series[1] == t["beta"][:n]
                             and series[2][: n - 1] == t["gamma"][: n - 1]}
