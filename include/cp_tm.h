@@ -236,6 +236,10 @@ int cp_server_step(cp_server *sv, int *n_active, int *n_queued, int *n_finished)
 int cp_server_result(cp_server *sv, uint64_t req_id, uint32_t *out_host, size_t out_len, int *state,
                      double times_s[3]);
 
+/* Withdraw a queued (not yet admitted) request; its state becomes -1.
+ * CP_EINVAL for an unknown id or a request already admitted. */
+int cp_server_cancel(cp_server *sv, uint64_t req_id);
+
 /* Ids of requests finished since the last poll (up to max_ids, oldest first). */
 int cp_server_poll(cp_server *sv, uint64_t *ids_out, int max_ids, int *n_ids);
 
@@ -264,6 +268,13 @@ const char *cp_last_error(void);
 /* For every rank r: unrank, check canonical form and membership, rank again;
  * *n_bad = number of ranks that fail, *size = size of the space. */
 int cp_debug_check_space(int kind, int m, int e, uint64_t *n_bad, uint64_t *size);
+
+/* Launch a wait that can never complete (an mbarrier nothing arrives on),
+ * bounded by `cycles` SM clock cycles, exactly like the bounded waits of the
+ * TMA gather kernel; returns CP_ETIMEOUT once it has expired (the device error
+ * word is read and cleared), leaving the context usable.  For testing the
+ * timeout path without faulting or hanging the GPU. */
+int cp_debug_wait_timeout(long long cycles);
 
 /* Partitions of the space in rank order, as canonical labels:
  * out_host[r*m + i] = block label of site i (first-occurrence order).

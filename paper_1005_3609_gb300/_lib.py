@@ -62,6 +62,8 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_double)]),
     "cp_server_release": (ctypes.c_int, [vp, ctypes.c_uint64]),
     "cp_server_poll": (ctypes.c_int, [vp, u64p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+    "cp_server_cancel": (ctypes.c_int, [vp, ctypes.c_uint64]),
+    "cp_debug_wait_timeout": (ctypes.c_int, [ctypes.c_longlong]),
     "cp_server_stats": (ctypes.c_int, [vp, u64p, u64p, u64p, ctypes.POINTER(ctypes.c_size_t)]),
     "cp_server_destroy": (None, [vp]),
     "cp_crt": (ctypes.c_int, [u32p, u32p, ctypes.c_int, ctypes.c_int, u32p, ctypes.c_int]),
@@ -346,6 +348,9 @@ class Server:
         n = ctypes.c_int()
         check("cp_server_poll", load().cp_server_poll(self._h, buf, max_ids, ctypes.byref(n)))
         return [int(buf[k]) for k in range(n.value)]
+
+    def cancel(self, rid):
+        check("cp_server_cancel", load().cp_server_cancel(self._h, rid))
 
     def release(self, rid):
         check("cp_server_release", load().cp_server_release(self._h, rid))

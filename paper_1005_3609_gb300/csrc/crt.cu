@@ -234,6 +234,7 @@ extern "C" int cp_select_primes(const uint64_t *draws, int n_draws, int n_primes
 // ------------------------------------------------------------------ diagnostics
 
 namespace cp {
+int debug_wait_timeout(long long cycles, cudaStream_t st);
 int check_space(int kind, int m, int e, uint64_t *n_bad, uint64_t *size);
 int enumerate_space(int kind, int m, int e, uint8_t *out_host, uint64_t max_states, uint64_t *size);
 }  // namespace cp
@@ -242,6 +243,11 @@ extern "C" int cp_debug_check_space(int kind, int m, int e, uint64_t *n_bad, uin
     if (m < 1 || m > CP_MAX_L || (kind != 0 && kind != 1) || (kind == 1 && (e < 0 || e + 1 >= m)))
         return fail(CP_EINVAL, "bad space");
     return check_space(kind, m, e, n_bad, size);
+}
+
+extern "C" int cp_debug_wait_timeout(long long cycles) {
+    if (cycles < 0 || cycles > (1ll << 33)) return fail(CP_EINVAL, "cycles must be in [0, 2^33]");
+    return debug_wait_timeout(cycles, 0);
 }
 
 extern "C" int cp_debug_enumerate_space(int kind, int m, int e, uint8_t *out_host, uint64_t max_states,

@@ -299,6 +299,22 @@ static int set_attrs() {
     return CP_OK;
 }
 
+// Diagnostic: a wait that can never complete (an mbarrier nothing arrives on),
+// bounded by `cycles`; on expiry it sets bit 16 of *err and returns, like the
+// gather kernels' waits.
+__global__ void wait_timeout_kernel(long long cycles, int *err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(smem_addr(&bar), 1);
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(smem_addr(&bar), 0, clock64() + cycles)) atomicOr(err, 1 << 16);
+}
+
+int debug_wait_timeout(long long cycles, cudaStream_t st) {
+    wait_timeout_kernel<<<1, 32, 0, st>>>(cycles, device_error_flag());
+    CP_CUDA_TRY(cudaGetLastError());
+    return check_device_error(st);
+}
+
 int prepare_gather_tma() {
     static bool done[64] = {};
     int dev = 0;

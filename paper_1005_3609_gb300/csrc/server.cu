@@ -427,6 +427,21 @@ extern "C" int cp_server_result(cp_server *sv, uint64_t req_id, uint32_t *out_ho
     return CP_OK;
 }
 
+extern "C" int cp_server_cancel(cp_server *sv, uint64_t req_id) {
+    if (!sv) return fail(CP_EINVAL, "server is NULL");
+    auto it = sv->reqs.find(req_id);
+    if (it == sv->reqs.end()) return fail(CP_EINVAL, "unknown request id");
+    Request *r = it->second.get();
+    if (r->state != REQ_QUEUED) return fail(CP_EINVAL, "only a queued request can be cancelled");
+    for (auto q = sv->queue.begin(); q != sv->queue.end(); ++q)
+        if (*q == r) {
+            sv->queue.erase(q);
+            break;
+        }
+    r->state = REQ_FAILED;
+    return CP_OK;
+}
+
 extern "C" int cp_server_poll(cp_server *sv, uint64_t *ids_out, int max_ids, int *n_ids) {
     if (!sv || !n_ids || (max_ids > 0 && !ids_out)) return fail(CP_EINVAL, "bad arguments");
     const int n = (int)std::min<size_t>((size_t)std::max(max_ids, 0), sv->finished.size());
