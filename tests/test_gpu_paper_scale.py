@@ -2,7 +2,8 @@
 
 The square sweep reproduces all of Table 1: alpha_k and beta_k for k = 0..79 (z^79 through
 the mu_40 term) and gamma_k for k = 0..78.  The triangular sweep reproduces Baxter's
-product, eq. (efb), and the printed series (efs_ser), (efc_ser) through x^40.
+product, eq. (efb), the printed series (efs_ser), (efc_ser) and the conjectured product
+formulae (efs), (efc) through x^40.
 Four primes suffice (the largest coefficient, |gamma_78|, is below 2^88).  The square sweep
 holds ~120 GB of state vectors on the device (the width-20 intermediate space has
 M_19 + M_18 = 24 735 666 states).
@@ -54,4 +55,7 @@ def test_triangular_k41_reproduces_baxter_and_printed(stream):
     assert bulk == flm.baxter_bulk(41)
     assert surf == tri["surface"]
     assert corner == tri["corner"]
+    # the conjectured product formulae, eqs. (efs) and (efc), through x^40
+    assert surf == flm.conjectured_surface(41)
+    assert corner == flm.conjectured_corner(41)
     cp.load().cp_clear_table_cache()
