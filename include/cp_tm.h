@@ -46,6 +46,8 @@ enum {
 
 #define CP_MAX_L 20       /* widest strip compiled in (the paper's m_max = 20, Sec. 4.2) */
 #define CP_MAX_PRIMES 32
+#define CP_POTTS_MAX_L 16 /* widest any-v Potts strip (Catalan(16) = 35,357,670 states) */
+#define CP_POTTS_MAX_V 16 /* |v| bound of the Potts strip (see cp_create_strip_potts) */
 
 typedef struct cp_strip cp_strip;
 
@@ -65,6 +67,31 @@ typedef struct cp_strip cp_strip;
  */
 int cp_create_strip(int lattice, int L, const uint32_t *primes_host, int n_primes,
                     int max_degree, int max_rows, void *cuda_stream, cp_strip **out);
+
+/*
+ * cp_create_strip_potts -- the same strip for the Potts partition function at
+ * any integer v (Sec. 3.1-3.2, the construction T = (prod_i V_i)(prod_i H_{i,i+1})
+ * before the chromatic specialisation): Z~(w) = q^{-|V|} Z(q, v) as a polynomial
+ * in w = 1/q, Z(q, v) = sum over edge subsets A of q^{k(A)} v^{|A|}, with
+ *   H_{i,i+1} = 1 + v J_{i,i+1},   V_i = v w + D_i,
+ * on all non-crossing partitions of the L sites (Catalan(L) states, no
+ * projector), triangular rectangles with the diagonals of Sec. 3.3.  At v = -1
+ * the residues equal those of cp_create_strip.  The strip is driven by the same
+ * calls (cp_advance_rows, cp_read_coeffs, cp_strip_info with n_states[0] =
+ * n_states[1] = Catalan(L), cp_strip_reset, cp_destroy).
+ *   v          integer coupling, |v| <= CP_POTTS_MAX_V; residues are taken mod
+ *              each prime, so v stands for its residue class
+ *   L          1..CP_POTTS_MAX_L
+ *   other arguments as cp_create_strip
+ * The transition coefficients (products of v and 1 + v) are packed beside a
+ * source index that needs ceil(log2 Catalan(L)) bits; the 30 - that many bits
+ * left hold the coefficient.  A v whose coefficients do not fit at this width
+ * is CP_EINVAL with a message saying so (wide strips take smaller |v|).
+ * Errors: CP_EINVAL (bad lattice/L/v/primes/D, coefficient too wide),
+ * CP_ENOMEM, CP_ECUDA, CP_ESTATE.
+ */
+int cp_create_strip_potts(int lattice, int L, int v, const uint32_t *primes_host, int n_primes,
+                          int max_degree, int max_rows, void *cuda_stream, cp_strip **out);
 
 /*
  * cp_advance_rows -- apply T = T_L ... T_1 n_rows times (eq. (T_sq_decomp));
@@ -262,7 +289,9 @@ const char *cp_last_error(void);
  * Checks of the rank/unrank bijection of Sec. 3.4 on the GPU.
  * kind 0 = NCNNN partitions of m points (size M_{m-1});
  * kind 1 = square-lattice space with the pair (e, e+1) excepted (0-based e),
- *          size M_{m-1} + M_{m-2}, NCNNN ranks first (Sec. 3.4, last paragraph).
+ *          size M_{m-1} + M_{m-2}, NCNNN ranks first (Sec. 3.4, last paragraph);
+ * kind 2 = all non-crossing partitions of m <= CP_POTTS_MAX_L points (the
+ *          Potts strip's space, size Catalan(m)).
  */
 
 /* For every rank r: unrank, check canonical form and membership, rank again;

@@ -33,6 +33,8 @@ class CPError(RuntimeError):
 SIGNATURES = {
     "cp_create_strip": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, u32p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        vp, ctypes.POINTER(vp)]),
+    "cp_create_strip_potts": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, u32p, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(vp)]),
     "cp_advance_rows": (ctypes.c_int, [vp, ctypes.c_int]),
     "cp_read_coeffs": (ctypes.c_int, [vp, u32p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int)]),
     "cp_read_coeffs_device": (ctypes.c_int, [vp, vp, ctypes.c_size_t]),
@@ -155,15 +157,25 @@ def crt_static(residues, primes, limbs_per_coeff=None):
 
 
 class Strip:
-    """A strip of width L (cp_create_strip / cp_advance_rows / cp_read_coeffs / cp_destroy)."""
+    """A strip of width L (cp_create_strip / cp_advance_rows / cp_read_coeffs / cp_destroy).
 
-    def __init__(self, lattice, L, primes, max_degree=-1, max_rows=1, stream=None):
+    With ``v`` given, the any-v Potts strip (cp_create_strip_potts): the
+    residues of Z~(w) = q^{-|V|} Z(q, v) instead of the chromatic P~.
+    """
+
+    def __init__(self, lattice, L, primes, max_degree=-1, max_rows=1, stream=None, v=None):
         pr, pp = _u32(primes)
         self.primes = [int(p) for p in pr]
         h = vp()
         s = stream if stream is None or isinstance(stream, int) else stream.cuda_stream
-        check("cp_create_strip", load().cp_create_strip(lattice_id(lattice), L, pp, len(pr), max_degree, max_rows,
-                                                        vp(s) if s else None, ctypes.byref(h)))
+        sh = vp(s) if s else None
+        if v is None:
+            check("cp_create_strip", load().cp_create_strip(lattice_id(lattice), L, pp, len(pr), max_degree,
+                                                            max_rows, sh, ctypes.byref(h)))
+        else:
+            check("cp_create_strip_potts", load().cp_create_strip_potts(lattice_id(lattice), L, int(v), pp, len(pr),
+                                                                        max_degree, max_rows, sh, ctypes.byref(h)))
+        self.v = v
         self._h = h
         ns = (ctypes.c_uint64 * 2)()
         deg, hgt = ctypes.c_int(), ctypes.c_int()

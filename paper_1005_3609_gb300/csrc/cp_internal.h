@@ -33,9 +33,14 @@ constexpr int kTblStride = kMaxN + 1;
 // cnt[n] = number of NCNNN partitions of n points (cnt[0] = 1, cnt[n] = M_{n-1});
 // off[n*kTblStride + k] = rank of the first n-point partition whose first point
 // has its smallest partner at relative position 2+k (eq. (M_recurs)).
+// cntc[n] = Catalan C_n (non-crossing partitions of n points), offc[n*kTblStride + k]
+// = rank of the first n-point non-crossing partition whose first point has its
+// smallest partner at relative position 1+k.
 struct RankTables {
     uint64_t cnt[kTblStride];
     uint64_t off[kTblStride * kTblStride];
+    uint64_t cntc[kTblStride];
+    uint64_t offc[kTblStride * kTblStride];
 };
 
 // A state space of one per-site factor.
@@ -45,7 +50,9 @@ struct RankTables {
 //           order, each NCNNN partition t in which e is alone and e-1 !~ e+1
 //           immediately followed by J_{e,e+1} t.  prefix[b] = number of such t
 //           with B-rank < b, so rank(t) = b + prefix[b] and rank(J t) = that + 1.
-enum SpaceKind : int32_t { SPACE_B = 0, SPACE_X = 1 };
+//  SPACE_C: all non-crossing partitions (the any-v Potts model, Sec. 3.2), in
+//           the order: first point alone first, then by its smallest partner.
+enum SpaceKind : int32_t { SPACE_B = 0, SPACE_X = 1, SPACE_C = 2 };
 struct Space {
     int32_t kind;
     int32_t m;      // number of sites
@@ -56,7 +63,10 @@ struct Space {
 };
 
 // Kind of per-site factor.
-enum OpKind : int32_t { OP_SQUARE = 0, OP_TRIANGULAR = 1, OP_LAST = 2, OP_IDENTITY = 3 };
+enum OpKind : int32_t {
+    OP_SQUARE = 0, OP_TRIANGULAR = 1, OP_LAST = 2, OP_IDENTITY = 3,  // chromatic (v = -1, projected)
+    OP_POTTS_SQUARE = 4, OP_POTTS_TRIANGULAR = 5, OP_POTTS_LAST = 6  // any v, no projectors
+};
 
 struct OpDesc {
     int32_t kind;
@@ -64,11 +74,22 @@ struct OpDesc {
     int32_t i;       // 0-based site
     int32_t max_terms;
     Space in, out;
+    int32_t v;         // Potts coupling (OP_POTTS_*)
+    int32_t src_bits;  // edge format of the table
 };
 
-// Packed CSR edge: src (27 bits) | shift << 27 (2 bits) | coef << 29 (3-bit two's complement)
+// Packed CSR edge: src (src_bits) | shift << src_bits (2 bits) | coef << (src_bits + 2)
+// (two's complement in the remaining bits).  Chromatic tables: 27 / 2 / 3 bits
+// (coefficients +1, -1, -2, -3).  Potts tables take as few source bits as the
+// space needs (at least 16), leaving 30 - src_bits bits for the coefficient.
 constexpr uint32_t kSrcBits = 27;
 constexpr uint32_t kSrcMask = (1u << kSrcBits) - 1u;
+constexpr uint32_t kPottsMinSrcBits = 16;
+inline int potts_src_bits(uint64_t n_states) {
+    int b = (int)kPottsMinSrcBits;
+    while (b < (int)kSrcBits && (1ull << b) - 1 < n_states) ++b;
+    return b;
+}
 
 // CSR-by-destination table of one per-site factor, on the device.
 struct SiteTable {
@@ -80,7 +101,7 @@ struct SiteTable {
 
 // All tables of one (lattice, L) on one device; shared between strips.
 struct TableSet {
-    int device = 0, lattice = 0, L = 0;
+    int device = 0, lattice = 0, L = 0, potts = 0, v = -1, src_bits = (int)kSrcBits;
     uint64_t S_b = 0, S_max = 0;
     std::vector<SiteTable> row;   // T_1..T_L
     std::vector<SiteTable> last;  // T_1^last..T_{L-1}^last (identity for L = 1)
@@ -95,8 +116,12 @@ int device_rank_tables(const RankTables **out_dev, RankTables *host_copy);
 // Prefix table of the interleaved space X_e on m sites (device, [M_{m-1} + 1]).
 int build_x_prefix(int m, int e, cudaStream_t st, uint32_t **out);
 
-// Build or fetch from the cache the tables of (lattice, L) on the current device.
+// Build or fetch from the cache the tables of (lattice, L) on the current device
+// (chromatic polynomial: the projected factorisation of Sec. 3.2-3.3).
 int get_tables(int lattice, int L, cudaStream_t stream, std::shared_ptr<TableSet> *out);
+// Tables of the any-v Potts transfer matrix T_i = V_i H_{i,i+1} (square) or
+// V_i H_{i-1,i} H_{i,i+1} (triangular) on non-crossing partitions.
+int get_potts_tables(int lattice, int L, int v, cudaStream_t stream, std::shared_ptr<TableSet> *out);
 
 // ------------------------------------------------------------------ gather
 // One per-site factor application: out[dst] = sum_e coef_e * w^{shift_e} in[src_e]  (mod p)
@@ -115,7 +140,8 @@ struct GatherTask {
     uint32_t n_primes;
     uint32_t c0;              // first chunk of the rows handled by this task
     uint32_t cw;              // chunks handled (a column range [c0, c0 + cw) of every row)
-    uint32_t pad[3];
+    uint32_t src_bits;        // edge format of the table
+    uint32_t pad[2];
 };
 
 constexpr int kGatherThreads = 256;  // 8 warps; one warp per destination row at a time

@@ -240,7 +240,8 @@ int enumerate_space(int kind, int m, int e, uint8_t *out_host, uint64_t max_stat
 }  // namespace cp
 
 extern "C" int cp_debug_check_space(int kind, int m, int e, uint64_t *n_bad, uint64_t *size) {
-    if (m < 1 || m > CP_MAX_L || (kind != 0 && kind != 1) || (kind == 1 && (e < 0 || e + 1 >= m)))
+    if (m < 1 || m > CP_MAX_L || kind < 0 || kind > 2 || (kind == 1 && (e < 0 || e + 1 >= m)) ||
+        (kind == 2 && m > CP_POTTS_MAX_L))
         return fail(CP_EINVAL, "bad space");
     return check_space(kind, m, e, n_bad, size);
 }
@@ -252,7 +253,8 @@ extern "C" int cp_debug_wait_timeout(long long cycles) {
 
 extern "C" int cp_debug_enumerate_space(int kind, int m, int e, uint8_t *out_host, uint64_t max_states,
                                         uint64_t *size) {
-    if (m < 1 || m > CP_MAX_L || (kind != 0 && kind != 1) || (kind == 1 && (e < 0 || e + 1 >= m)))
+    if (m < 1 || m > CP_MAX_L || kind < 0 || kind > 2 || (kind == 1 && (e < 0 || e + 1 >= m)) ||
+        (kind == 2 && m > CP_POTTS_MAX_L))
         return fail(CP_EINVAL, "bad space");
     return enumerate_space(kind, m, e, out_host, max_states, size);
 }

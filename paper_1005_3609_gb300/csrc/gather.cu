@@ -32,8 +32,9 @@ __device__ __forceinline__ uint32_t reduce_s64(long long v, uint32_t p, float in
     return min(r, r - p);                        // >= p     -> - p
 }
 
-__device__ __forceinline__ int edge_coef(uint32_t e) { return ((int)(e >> 29) << 29) >> 29; }
-__device__ __forceinline__ uint32_t edge_shift(uint32_t e) { return (e >> kSrcBits) & 3u; }
+__device__ __forceinline__ int edge_coef(uint32_t e, uint32_t sb) { return (int)e >> (sb + 2); }
+__device__ __forceinline__ uint32_t edge_shift(uint32_t e, uint32_t sb) { return (e >> sb) & 3u; }
+__device__ __forceinline__ uint32_t edge_src(uint32_t e, uint32_t sb) { return e & ((1u << sb) - 1u); }
 __device__ __forceinline__ uint32_t fast_div(uint32_t x, uint32_t magic) { return magic ? __umulhi(x, magic) : x; }
 
 constexpr int kWarps = kGatherThreads / 32;
@@ -50,17 +51,17 @@ __device__ __forceinline__ void gather_edges(const GatherTask &t, uint32_t my, i
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             q[j] = __shfl_sync(kFull, my, min(e + j, 31));
-            const uint32_t sh = edge_shift(q[j]);
+            const uint32_t sh = edge_shift(q[j], t.src_bits);
             x[j] = make_uint4(0, 0, 0, 0);
             if (e + j < n && active && deg >= sh) {
-                const size_t off = (size_t)(q[j] & kSrcMask) * t.C + (c - sh * t.cpd);
+                const size_t off = (size_t)edge_src(q[j], t.src_bits) * t.C + (c - sh * t.cpd);
                 if (V4) x[j] = __ldg(reinterpret_cast<const uint4 *>(t.in) + off);
                 else x[j].x = __ldg(t.in + off);
             }
         }
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const long long cf = edge_coef(q[j]);  // absent edges loaded zero
+            const long long cf = edge_coef(q[j], t.src_bits);  // absent edges loaded zero
             acc[0] += (long long)(int)x[j].x * cf;
             if (V4) {
                 acc[1] += (long long)(int)x[j].y * cf;
@@ -197,6 +198,7 @@ void append_gather_tasks(std::vector<GatherTask> *tasks, const SiteTable &tab, c
     t.vec4 = v4 ? 1 : 0;
     t.magic_cpd = magic_for(t.cpd);
     t.n_primes = (uint32_t)P;
+    t.src_bits = (uint32_t)tab.op.src_bits;
     const uint32_t ncol = v4 ? (t.C + 255) / 256 : 1;
     for (uint32_t k = 0; k < ncol; ++k) {  // balanced column ranges
         t.c0 = (uint32_t)((uint64_t)t.C * k / ncol);

@@ -177,14 +177,14 @@ __global__ void __launch_bounds__(kTmaThreads, PASSES == 1 ? 4 : (PASSES == 2 ? 
                     }
                     if (ok) {
                         meta[s] = qj;
-                        const uint32_t back = ((qj >> kSrcBits) & 3u) * t.cpd;  // shift in chunks
+                        const uint32_t back = ((qj >> t.src_bits) & 3u) * t.cpd;  // shift in chunks
                         const uint32_t skip = back > t.c0 ? min(back - t.c0, t.cw) : 0u;
                         const uint32_t bytes = (t.cw - skip) * 16u;
                         const uint32_t fb = smem_addr(&full_bar[s]);
                         if (bytes) {
                             mbar_arrive_expect_tx(fb, bytes);
                             bulk_copy_g2s(smem_addr(smem + (size_t)s * RB + skip * 16u),
-                                          in_bytes + (size_t)(qj & kSrcMask) * src_row_bytes +
+                                          in_bytes + (size_t)(qj & ((1u << t.src_bits) - 1u)) * src_row_bytes +
                                               (size_t)(t.c0 + skip - back) * 16u,
                                           bytes, fb);
                         } else {
@@ -236,8 +236,8 @@ __global__ void __launch_bounds__(kTmaThreads, PASSES == 1 ? 4 : (PASSES == 2 ? 
                 return;
             }
             const uint32_t q = meta[s];
-            const uint32_t sh = (q >> kSrcBits) & 3u;
-            const long long cf = ((int)(q >> 29) << 29) >> 29;
+            const uint32_t sh = (q >> t.src_bits) & 3u;
+            const long long cf = (int)q >> (t.src_bits + 2);
             const uint4 *sd = reinterpret_cast<const uint4 *>(smem + (size_t)s * RB);
 #pragma unroll
             for (int p = 0; p < PASSES; ++p) {

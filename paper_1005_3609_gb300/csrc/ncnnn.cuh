@@ -141,6 +141,64 @@ __device__ __forceinline__ void ncnnn_unrank(uint64_t r, int lo, int hi, Labels 
     }
 }
 
+// Rank of a non-crossing partition of points lo..hi-1: the first point alone
+// first (rank of the rest), then by its smallest partner lo+1+k, inner points
+// as the most significant digit and the right part (from the partner on) as
+// the least significant one.  The count recursion is Catalan's.
+__device__ __forceinline__ uint64_t nc_rank(const Labels &s, int lo, int hi, const RankTables &T) {
+    int sa[kMaxL + 1], sb[kMaxL + 1];
+    uint64_t smul[kMaxL + 1];
+    int sp = 0;
+    uint64_t r = 0;
+    int a = lo, b = hi;
+    uint64_t mu = 1;
+    for (;;) {
+        while (b - a > 1) {
+            int n = b - a, j = -1;
+            for (int t = a + 1; t < b; ++t)
+                if (s.v[t] == s.v[a]) { j = t; break; }
+            if (j < 0) { ++a; continue; }
+            int k = j - a - 1;
+            r += mu * T.offc[n * kTblStride + k];
+            sa[sp] = a + 1; sb[sp] = j; smul[sp] = mu * T.cntc[b - j]; ++sp;  // inner part, later
+            a = j;                                                              // right part, now
+        }
+        if (sp == 0) break;
+        --sp;
+        a = sa[sp]; b = sb[sp]; mu = smul[sp];
+    }
+    return r;
+}
+
+__device__ __forceinline__ void nc_unrank(uint64_t r, int lo, int hi, Labels &s, const RankTables &T) {
+    for (int i = lo; i < hi; ++i) s.v[i] = 0xFF;
+    uint8_t next = 0;
+    int sa[kMaxL + 1], sb[kMaxL + 1];
+    uint64_t sr[kMaxL + 1];
+    int sp = 0;
+    int a = lo, b = hi;
+    for (;;) {
+        while (b - a >= 1) {
+            if (s.v[a] == 0xFF) s.v[a] = next++;
+            int n = b - a;
+            if (n == 1) break;
+            if (r < T.cntc[n - 1]) { ++a; continue; }  // point a alone
+            int k = 0;
+            while (k + 1 <= n - 2 && T.offc[n * kTblStride + k + 1] <= r) ++k;
+            r -= T.offc[n * kTblStride + k];
+            uint64_t cr = T.cntc[n - 1 - k];
+            uint64_t inner = r / cr, right = r - inner * cr;
+            int j = a + 1 + k;
+            s.v[j] = s.v[a];
+            sa[sp] = j; sb[sp] = b; sr[sp] = right; ++sp;  // right part after the inner one
+            a = a + 1; b = j; r = inner;
+        }
+        if (sp == 0) break;
+        --sp;
+        a = sa[sp]; b = sb[sp]; r = sr[sp];
+    }
+}
+
 // Rank in a space (SPACE_B: the paper's order; SPACE_X: the interleaved order,
 // see Space).  Returns ~0ull for a partition outside the space's rule.
 __device__ __forceinline__ uint64_t space_rank(const Labels &s, const Space &sp, const RankTables &T) {
@@ -156,6 +214,7 @@ __device__ __forceinline__ uint64_t space_rank(const Labels &s, const Space &sp,
         uint64_t b = ncnnn_rank(s, 0, m, T);
         return b == ~0ull ? b : b + sp.prefix[b];
     }
+    if (sp.kind == SPACE_C) return nc_rank(s, 0, m, T);
     return ncnnn_rank(s, 0, m, T);
 }
 
@@ -172,11 +231,16 @@ __device__ __forceinline__ void space_unrank(uint64_t r, const Space &sp, Labels
         if (r != lo + sp.prefix[lo]) join_blocks(s, m, sp.e, sp.e + 1);
         return;
     }
+    if (sp.kind == SPACE_C) {
+        nc_unrank(r, 0, m, s, T);
+        return;
+    }
     ncnnn_unrank(r, 0, m, s, T);
 }
 
 // Membership test of a canonical partition in a space (debug/validation).
 __device__ __forceinline__ bool space_contains(const Labels &s, const Space &sp) {
+    if (sp.kind == SPACE_C) return is_noncrossing(s, sp.m);
     return is_noncrossing(s, sp.m) && nn_ok(s, sp.m, sp.kind == SPACE_X ? sp.e : -1);
 }
 

@@ -123,8 +123,8 @@ static uint32_t list_blocks(const std::vector<GatherTask> &l, int tile) {
     return n;
 }
 
-extern "C" int cp_create_strip(int lattice, int L, const uint32_t *primes, int n_primes, int max_degree,
-                               int max_rows, void *cuda_stream, cp_strip **out) {
+static int check_strip_args(int lattice, int L, const uint32_t *primes, int n_primes, int max_degree, int max_rows,
+                            cp_strip **out) {
     if (!out) return fail(CP_EINVAL, "out is NULL");
     *out = nullptr;
     if (lattice != CP_SQUARE && lattice != CP_TRIANGULAR) return fail(CP_EINVAL, "lattice must be CP_SQUARE or CP_TRIANGULAR");
@@ -135,6 +135,14 @@ extern "C" int cp_create_strip(int lattice, int L, const uint32_t *primes, int n
     if (rc) return rc;
     long long D = max_degree >= 0 ? max_degree : (long long)L * max_rows - 1;
     if (D + 1 > (1 << 20)) return fail(CP_EINVAL, "degree too large");
+    return CP_OK;
+}
+
+// The strip around a table set: state vectors, read-out scratch, precomputed launches.
+static int make_strip(std::shared_ptr<TableSet> tabs, int lattice, int L, const uint32_t *primes, int n_primes,
+                      int max_degree, int max_rows, void *cuda_stream, cp_strip **out) {
+    int rc = CP_OK;
+    long long D = max_degree >= 0 ? max_degree : (long long)L * max_rows - 1;
     auto s = std::make_unique<cp_strip>();
     s->lattice = lattice;
     s->L = L;
@@ -142,8 +150,7 @@ extern "C" int cp_create_strip(int lattice, int L, const uint32_t *primes, int n
     s->D1 = (int)D + 1;
     s->max_rows = max_rows;
     s->stream = (cudaStream_t)cuda_stream;
-    if ((rc = prepare_gather_kernels())) return rc;
-    if ((rc = get_tables(lattice, L, s->stream, &s->tabs))) return rc;
+    s->tabs = std::move(tabs);
     const TableSet &ts = *s->tabs;
     const size_t row_words = (size_t)s->D1 * s->P;
     if ((rc = dev_alloc((void **)&s->primes_dev, 4 * CP_MAX_PRIMES))) return rc;
@@ -201,6 +208,28 @@ extern "C" int cp_create_strip(int lattice, int L, const uint32_t *primes, int n
     s->height = 1;
     *out = s.release();
     return CP_OK;
+}
+
+extern "C" int cp_create_strip(int lattice, int L, const uint32_t *primes, int n_primes, int max_degree,
+                               int max_rows, void *cuda_stream, cp_strip **out) {
+    int rc = check_strip_args(lattice, L, primes, n_primes, max_degree, max_rows, out);
+    if (rc) return rc;
+    if ((rc = prepare_gather_kernels())) return rc;
+    std::shared_ptr<TableSet> tabs;
+    if ((rc = get_tables(lattice, L, (cudaStream_t)cuda_stream, &tabs))) return rc;
+    return make_strip(std::move(tabs), lattice, L, primes, n_primes, max_degree, max_rows, cuda_stream, out);
+}
+
+extern "C" int cp_create_strip_potts(int lattice, int L, int v, const uint32_t *primes, int n_primes, int max_degree,
+                                     int max_rows, void *cuda_stream, cp_strip **out) {
+    int rc = check_strip_args(lattice, L, primes, n_primes, max_degree, max_rows, out);
+    if (rc) return rc;
+    if (v < -CP_POTTS_MAX_V || v > CP_POTTS_MAX_V) return fail(CP_EINVAL, "v must be in [-CP_POTTS_MAX_V, CP_POTTS_MAX_V]");
+    if (L > CP_POTTS_MAX_L) return fail(CP_EINVAL, "L must be 1..CP_POTTS_MAX_L for the Potts strip");
+    if ((rc = prepare_gather_kernels())) return rc;
+    std::shared_ptr<TableSet> tabs;
+    if ((rc = get_potts_tables(lattice, L, v, (cudaStream_t)cuda_stream, &tabs))) return rc;
+    return make_strip(std::move(tabs), lattice, L, primes, n_primes, max_degree, max_rows, cuda_stream, out);
 }
 
 extern "C" int cp_advance_rows(cp_strip *s, int n_rows) {

@@ -12,6 +12,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <utility>
 
 #include "cp_internal.h"
@@ -42,14 +43,29 @@ __global__ void rank_tables_kernel(RankTables *T) {
             o += T->cnt[k + 1] * T->cnt[n - k - 2];
         }
     }
+    // Catalan numbers and the offsets of the non-crossing order (partner at 1+k)
+    T->cntc[0] = 1;
+    for (int n = 1; n < kTblStride; ++n) {
+        uint64_t c = 0;
+        for (int k = 0; k < n; ++k) c += T->cntc[k] * T->cntc[n - 1 - k];
+        T->cntc[n] = c;
+    }
+    for (int k = 0; k < kTblStride * kTblStride; ++k) T->offc[k] = 0;
+    for (int n = 2; n < kTblStride; ++n) {
+        uint64_t o = T->cntc[n - 1];
+        for (int k = 0; k <= n - 2; ++k) {
+            T->offc[n * kTblStride + k] = o;
+            o += T->cntc[k] * T->cntc[n - 1 - k];
+        }
+    }
 }
 
 // ------------------------------------------------------------------ term generation
 
 struct Term {
     Labels s;
-    int8_t coef;
-    int8_t shift;
+    int32_t coef;
+    int32_t shift;
 };
 
 constexpr int kMaxTerms = 8;
@@ -62,7 +78,7 @@ __device__ int op_h(Term *t, int n, int m, int a, int b) {
         if (t[j].s.v[a] == t[j].s.v[b]) { t[j].coef = 0; continue; }
         Term u = t[j];
         join_blocks(u.s, m, a, b);
-        u.coef = (int8_t)-u.coef;
+        u.coef = -u.coef;
         u.shift += 1;
         t[k++] = u;
     }
@@ -76,7 +92,7 @@ __device__ int op_h(Term *t, int n, int m, int a, int b) {
 __device__ int op_v(Term *t, int n, int m, int i) {
     for (int j = 0; j < n; ++j) {
         Term u = t[j];
-        u.coef = (int8_t)-u.coef;
+        u.coef = -u.coef;
         u.shift += 1;
         t[n + j] = u;
         detach_site(t[j].s, m, i);
@@ -98,6 +114,41 @@ __device__ int op_p(Term *t, int n, int lo, int hi, int skip) {
             if (q != skip && t[j].s.v[q] == t[j].s.v[q + 1]) { ok = false; break; }
         if (ok) t[w++] = t[j];
     }
+    return w;
+}
+
+// Any-v operators (Sec. 3.1): H_{a,b} = 1 + v J_{a,b}, where J is the identity
+// (no w) when a ~ b and joins with a factor w otherwise; V_i = v w + D_i.
+__device__ int op_hv(Term *t, int n, int m, int a, int b, int v) {
+    int k = n;
+    for (int j = 0; j < n; ++j) {
+        if (t[j].s.v[a] == t[j].s.v[b]) {
+            t[j].coef *= (1 + v);
+            continue;
+        }
+        Term u = t[j];
+        join_blocks(u.s, m, a, b);
+        u.coef *= v;
+        u.shift += 1;
+        t[k++] = u;
+    }
+    int w = 0;
+    for (int j = 0; j < k; ++j)
+        if (t[j].coef != 0) t[w++] = t[j];
+    return w;
+}
+
+__device__ int op_vv(Term *t, int n, int m, int i, int v) {
+    for (int j = 0; j < n; ++j) {
+        Term u = t[j];
+        u.coef *= v;
+        u.shift += 1;
+        t[n + j] = u;
+        detach_site(t[j].s, m, i);
+    }
+    int w = 0;
+    for (int j = 0; j < 2 * n; ++j)
+        if (t[j].coef != 0) t[w++] = t[j];
     return w;
 }
 
@@ -123,6 +174,19 @@ __device__ int factor_terms(const OpDesc &op, const Labels &s, Term *t) {
             if (i < m - 1) n = op_h(t, n, m, i, i + 1);
             n = op_d(t, n, m, i);
             n = op_p(t, n, i + 1, m - 1, -1);
+            break;
+        case OP_POTTS_SQUARE:  // V_i H_{i,i+1}: the rows of T = (prod V)(prod H), Sec. 3.2
+            if (i < m - 1) n = op_hv(t, n, m, i, i + 1, op.v);
+            n = op_vv(t, n, m, i, op.v);
+            break;
+        case OP_POTTS_TRIANGULAR:  // V_i H_{i-1,i} H_{i,i+1} (H_{i-1,i}: the diagonal, Sec. 3.3)
+            if (i < m - 1) n = op_hv(t, n, m, i, i + 1, op.v);
+            if (i > 0) n = op_hv(t, n, m, i - 1, i, op.v);
+            n = op_vv(t, n, m, i, op.v);
+            break;
+        case OP_POTTS_LAST:  // D_i H_{i,i+1}: last horizontal edges; every state ends at e_0
+            if (i < m - 1) n = op_hv(t, n, m, i, i + 1, op.v);
+            n = op_d(t, n, m, i);
             break;
         default:  // identity
             break;
@@ -157,18 +221,20 @@ __global__ void build_terms_kernel(OpDesc op, const RankTables *Tg, uint32_t *sl
         if (t[j].coef == 0 || dst[j] == ~0u) continue;
         for (int q = j + 1; q < n; ++q)
             if (dst[q] == dst[j] && t[q].shift == t[j].shift && t[q].coef != 0) {
-                t[j].coef = (int8_t)(t[j].coef + t[q].coef);
+                t[j].coef += t[q].coef;
                 t[q].coef = 0;
             }
     }
+    const int sb = op.src_bits, cb = 30 - sb;  // coefficient bits
+    const int cmin = -(1 << (cb - 1)), cmax = (1 << (cb - 1)) - 1;
     int w = 0;
     for (int j = 0; j < n; ++j) {
         if (t[j].coef == 0 || dst[j] == ~0u) continue;
-        if (t[j].coef < -4 || t[j].coef > 3) { bad |= 4; continue; }
+        if (t[j].coef < cmin || t[j].coef > cmax || t[j].shift > 3) { bad |= 4; continue; }
         if (w >= K) { bad |= 2; break; }
         slot_dst[src * K + w] = dst[j];
-        slot_edge[src * K + w] = (uint32_t)src | ((uint32_t)t[j].shift << kSrcBits) |
-                                 (((uint32_t)t[j].coef & 7u) << (kSrcBits + 2));
+        slot_edge[src * K + w] = (uint32_t)src | ((uint32_t)t[j].shift << sb) |
+                                 (((uint32_t)t[j].coef & ((1u << cb) - 1u)) << (sb + 2));
         ++w;
     }
     for (; w < K; ++w) slot_dst[src * K + w] = ~0u;
@@ -346,7 +412,8 @@ static int build_table(const OpDesc &op, const RankTables *T_dev, cudaStream_t s
     tab->op = op;
     tab->n_src = op.in.size;
     tab->n_dst = op.out.size;
-    if (op.in.size > kSrcMask || op.out.size >= 0xFFFFFFFFull) return fail(CP_EINVAL, "state space too large");
+    if (op.in.size > ((1ull << op.src_bits) - 1) || op.out.size >= 0xFFFFFFFFull)
+        return fail(CP_EINVAL, "state space too large for the edge format");
     const int K = op.max_terms;
     uint64_t n_slots = op.in.size * (uint64_t)K;
     uint32_t *slot_dst = nullptr, *slot_edge = nullptr, *cnt = nullptr, *cursor = nullptr;
@@ -393,6 +460,11 @@ static int build_table(const OpDesc &op, const RankTables *T_dev, cudaStream_t s
         cleanup();
         return fail(CP_ECUDA, std::string("table build: ") + cudaGetErrorString(e));
     }
+    if (herr == 4) {
+        cleanup();
+        return fail(CP_EINVAL, "a transition coefficient does not fit the " + std::to_string(30 - op.src_bits) +
+                                   "-bit field of this width's edge format (|v| too large)");
+    }
     if (herr) {
         cleanup();
         return fail(CP_ESTATE, "transition table check failed (flags " + std::to_string(herr) + ") for op kind " +
@@ -430,6 +502,7 @@ static int identity_table(int m, SiteTable *tab) {
     OpDesc op{};
     op.kind = OP_IDENTITY;
     op.m = m;
+    op.src_bits = (int)kSrcBits;
     op.in = Space{SPACE_B, m, 0, 0, 1, nullptr};
     op.out = op.in;
     tab->op = op;
@@ -468,6 +541,7 @@ static int build_tableset(int lattice, int L, cudaStream_t st, std::shared_ptr<T
         OpDesc op{};
         op.m = L;
         op.i = i;
+        op.src_bits = (int)kSrcBits;
         if (lattice == CP_SQUARE) {
             op.kind = OP_SQUARE;
             op.max_terms = 4;
@@ -494,6 +568,7 @@ static int build_tableset(int lattice, int L, cudaStream_t st, std::shared_ptr<T
             op.kind = OP_LAST;
             op.m = L;
             op.i = i;
+            op.src_bits = (int)kSrcBits;
             op.max_terms = 2;
             op.in = Space{SPACE_B, L, 0, 0, T.cnt[L - i], nullptr};
             op.out = Space{SPACE_B, L, 0, 0, T.cnt[L - i - 1], nullptr};
@@ -507,8 +582,64 @@ static int build_tableset(int lattice, int L, cudaStream_t st, std::shared_ptr<T
     return CP_OK;
 }
 
+// Any-v Potts tables on the non-crossing partitions (Catalan space), no projectors.
+static int build_potts_tableset(int lattice, int L, int v, cudaStream_t st, std::shared_ptr<TableSet> *out) {
+    const RankTables *T_dev = nullptr;
+    RankTables T;
+    int rc = device_rank_tables(&T_dev, &T);
+    if (rc) return rc;
+    auto ts = std::make_shared<TableSet>();
+    cudaGetDevice(&ts->device);
+    ts->lattice = lattice;
+    ts->L = L;
+    ts->potts = 1;
+    ts->v = v;
+    const uint64_t S = T.cntc[L];
+    ts->src_bits = potts_src_bits(S);
+    ts->S_b = ts->S_max = S;
+    for (int i = 0; i < L; ++i) {
+        OpDesc op{};
+        op.kind = lattice == CP_SQUARE ? OP_POTTS_SQUARE : OP_POTTS_TRIANGULAR;
+        op.m = L;
+        op.i = i;
+        op.v = v;
+        op.src_bits = ts->src_bits;
+        op.max_terms = lattice == CP_SQUARE ? 4 : 8;
+        op.in = Space{SPACE_C, L, 0, 0, S, nullptr};
+        op.out = op.in;
+        SiteTable tab;
+        if ((rc = build_table(op, T_dev, st, &tab))) return rc;
+        ts->bytes += (tab.n_dst + 1 + tab.nnz) * 4;
+        ts->row.push_back(tab);
+    }
+    if (L == 1) {
+        SiteTable tab;
+        if ((rc = identity_table(1, &tab))) return rc;
+        ts->last.push_back(tab);
+    } else {
+        for (int i = 0; i + 1 < L; ++i) {  // D_L is the identity on e_0
+            OpDesc op{};
+            op.kind = OP_POTTS_LAST;
+            op.m = L;
+            op.i = i;
+            op.v = v;
+            op.src_bits = ts->src_bits;
+            op.max_terms = 2;
+            op.in = Space{SPACE_C, L, 0, 0, T.cntc[L - i], nullptr};
+            op.out = Space{SPACE_C, L, 0, 0, T.cntc[L - i - 1], nullptr};
+            SiteTable tab;
+            if ((rc = build_table(op, T_dev, st, &tab))) return rc;
+            ts->bytes += (tab.n_dst + 1 + tab.nnz) * 4;
+            ts->last.push_back(tab);
+        }
+    }
+    *out = ts;
+    return CP_OK;
+}
+
 static std::mutex g_cache_mu;
 static std::map<std::pair<int, int>, std::shared_ptr<TableSet>> g_cache[64];  // per device
+static std::map<std::tuple<int, int, int>, std::shared_ptr<TableSet>> g_potts_cache[64];
 
 int get_tables(int lattice, int L, cudaStream_t st, std::shared_ptr<TableSet> *out) {
     int dev = 0;
@@ -529,9 +660,29 @@ int get_tables(int lattice, int L, cudaStream_t st, std::shared_ptr<TableSet> *o
     return CP_OK;
 }
 
+int get_potts_tables(int lattice, int L, int v, cudaStream_t st, std::shared_ptr<TableSet> *out) {
+    int dev = 0;
+    CP_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(CP_EINVAL, "device index");
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto key = std::make_tuple(lattice, L, v);
+    auto it = g_potts_cache[dev].find(key);
+    if (it != g_potts_cache[dev].end()) {
+        *out = it->second;
+        return CP_OK;
+    }
+    std::shared_ptr<TableSet> ts;
+    int rc = build_potts_tableset(lattice, L, v, st, &ts);
+    if (rc) return rc;
+    g_potts_cache[dev][key] = ts;
+    *out = ts;
+    return CP_OK;
+}
+
 void clear_table_cache() {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     for (auto &c : g_cache) c.clear();  // strips keep their own shared_ptr alive
+    for (auto &c : g_potts_cache) c.clear();
 }
 
 static std::mutex g_rt_mu;
@@ -578,7 +729,8 @@ int check_space(int kind, int m, int e, uint64_t *n_bad, uint64_t *size) {
     RankTables T;
     int rc = device_rank_tables(&T_dev, &T);
     if (rc) return rc;
-    Space sp{kind, m, e, 0, kind == SPACE_X ? T.cnt[m] + T.cnt[m - 1] : T.cnt[m], nullptr};
+    Space sp{kind, m, e, 0, kind == SPACE_X ? T.cnt[m] + T.cnt[m - 1] : (kind == SPACE_C ? T.cntc[m] : T.cnt[m]),
+             nullptr};
     uint32_t *pre = nullptr;
     if (kind == SPACE_X && (rc = build_x_prefix(m, e, 0, &pre))) return rc;
     sp.prefix = pre;
@@ -615,7 +767,8 @@ int enumerate_space(int kind, int m, int e, uint8_t *out_host, uint64_t max_stat
     RankTables T;
     int rc = device_rank_tables(&T_dev, &T);
     if (rc) return rc;
-    Space sp{kind, m, e, 0, kind == SPACE_X ? T.cnt[m] + T.cnt[m - 1] : T.cnt[m], nullptr};
+    Space sp{kind, m, e, 0, kind == SPACE_X ? T.cnt[m] + T.cnt[m - 1] : (kind == SPACE_C ? T.cntc[m] : T.cnt[m]),
+             nullptr};
     *size = sp.size;
     if (sp.size > max_states) return fail(CP_EINVAL, "output buffer too small");
     uint32_t *pre = nullptr;
