@@ -23,13 +23,15 @@
 
 namespace cp {
 
-// v mod p for |v| < 2^40: floor(v/p) from a float estimate (off by at most
-// one), then an exact 32-bit correction.
+// v mod p for |v| < p * sum|coef| <= p * 2^20 (the table build enforces the
+// bound).  The quotient estimate fl(fl(v) * fl(1/p) - 1/2), fused, is within
+// 1/4 of v/p - 1/2 (relative error of the product < 3 * 2^-24 on |v/p| < 2^20,
+// plus half an ulp below 2^20), so its floor q' gives v - q' p in (p/4, 7p/4),
+// below 2^32 for p < 2^31, and one conditional subtraction finishes.
 __device__ __forceinline__ uint32_t reduce_s64(long long v, uint32_t p, float invp) {
-    const int q = __float2int_rd(__ll2float_rn(v) * invp);
-    uint32_t r = (uint32_t)v - (uint32_t)q * p;  // exact value lies in [-p, 2p)
-    r = min(r, r + p);                           // negative -> + p
-    return min(r, r - p);                        // >= p     -> - p
+    const int q = __float2int_rd(__fmaf_rn(__ll2float_rn(v), invp, -0.5f));
+    const uint32_t r = (uint32_t)v - (uint32_t)q * p;
+    return min(r, r - p);
 }
 
 __device__ __forceinline__ int edge_coef(uint32_t e, uint32_t sb) { return (int)e >> (sb + 2); }

@@ -243,12 +243,26 @@ __global__ void build_terms_kernel(OpDesc op, const RankTables *Tg, uint32_t *sl
 
 // ------------------------------------------------------------------ CSR by destination
 
-__global__ void count_kernel(const uint32_t *slot_dst, uint64_t n_slots, uint32_t *cnt) {
+// Edges per destination, and sum of |coef| per destination into csum.
+__global__ void count_kernel(const uint32_t *slot_dst, const uint32_t *slot_edge, uint64_t n_slots, int src_bits,
+                             uint32_t *cnt, uint32_t *csum) {
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_slots;
          k += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t d = slot_dst[k];
-        if (d != ~0u) atomicAdd(&cnt[d], 1u);
+        if (d == ~0u) continue;
+        atomicAdd(&cnt[d], 1u);
+        const int c = (int)slot_edge[k] >> (src_bits + 2);
+        atomicAdd(&csum[d], (uint32_t)(c < 0 ? -c : c));
     }
+}
+
+// Largest entry of cnt (warp maximum, one atomic per warp).
+__global__ void max_count_kernel(const uint32_t *cnt, uint64_t n, int *out) {
+    uint32_t m = 0;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x)
+        m = max(m, cnt[k]);
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (int)m);
 }
 
 constexpr int kScanThreads = 1024;
@@ -416,7 +430,7 @@ static int build_table(const OpDesc &op, const RankTables *T_dev, cudaStream_t s
         return fail(CP_EINVAL, "state space too large for the edge format");
     const int K = op.max_terms;
     uint64_t n_slots = op.in.size * (uint64_t)K;
-    uint32_t *slot_dst = nullptr, *slot_edge = nullptr, *cnt = nullptr, *cursor = nullptr;
+    uint32_t *slot_dst = nullptr, *slot_edge = nullptr, *cnt = nullptr, *cursor = nullptr, *csum = nullptr;
     int *err = nullptr;
     int rc = CP_OK;
     auto cleanup = [&]() {
@@ -424,11 +438,13 @@ static int build_table(const OpDesc &op, const RankTables *T_dev, cudaStream_t s
         dev_free(slot_edge);
         dev_free(cnt);
         dev_free(cursor);
+        dev_free(csum);
         dev_free(err);
     };
     if ((rc = dev_alloc((void **)&slot_dst, n_slots * 4)) || (rc = dev_alloc((void **)&slot_edge, n_slots * 4)) ||
         (rc = dev_alloc((void **)&cnt, op.out.size * 4)) || (rc = dev_alloc((void **)&cursor, op.out.size * 4)) ||
-        (rc = dev_alloc((void **)&err, sizeof(int)))) {
+        (rc = dev_alloc((void **)&csum, op.out.size * 4)) ||
+        (rc = dev_alloc((void **)&err, 2 * sizeof(int)))) {
         cleanup();
         return rc;
     }
@@ -438,10 +454,12 @@ static int build_table(const OpDesc &op, const RankTables *T_dev, cudaStream_t s
     }
     cudaMemsetAsync(cnt, 0, op.out.size * 4, st);
     cudaMemsetAsync(cursor, 0, op.out.size * 4, st);
-    cudaMemsetAsync(err, 0, sizeof(int), st);
+    cudaMemsetAsync(csum, 0, op.out.size * 4, st);
+    cudaMemsetAsync(err, 0, 2 * sizeof(int), st);
     const int bt = 128;
     build_terms_kernel<<<(unsigned)((op.in.size + bt - 1) / bt), bt, 0, st>>>(op, T_dev, slot_dst, slot_edge, K, err);
-    count_kernel<<<1216, 256, 0, st>>>(slot_dst, n_slots, cnt);
+    count_kernel<<<1216, 256, 0, st>>>(slot_dst, slot_edge, n_slots, op.src_bits, cnt, csum);
+    max_count_kernel<<<608, 256, 0, st>>>(csum, op.out.size, err + 1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         cleanup();
@@ -451,23 +469,30 @@ static int build_table(const OpDesc &op, const RankTables *T_dev, cudaStream_t s
         cleanup();
         return rc;
     }
-    int herr = 0;
+    int herr[2] = {0, 0};
     uint32_t nnz = 0;
-    cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(herr, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(&nnz, tab->row_ptr + op.out.size, 4, cudaMemcpyDeviceToHost, st);
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         cleanup();
         return fail(CP_ECUDA, std::string("table build: ") + cudaGetErrorString(e));
     }
-    if (herr == 4) {
+    // The gathers reduce sum_e coef_e x_e (x_e < p) with a float estimate of the
+    // quotient (three roundings, relative error < 2^-22), exact while the
+    // quotient's magnitude, at most sum_e |coef_e|, stays below 2^20.
+    if (herr[0] == 0 && herr[1] >= (1 << 20)) {
+        cleanup();
+        return fail(CP_EINVAL, "too many transitions into one state for the exact modular reduction");
+    }
+    if (herr[0] == 4) {
         cleanup();
         return fail(CP_EINVAL, "a transition coefficient does not fit the " + std::to_string(30 - op.src_bits) +
                                    "-bit field of this width's edge format (|v| too large)");
     }
-    if (herr) {
+    if (herr[0]) {
         cleanup();
-        return fail(CP_ESTATE, "transition table check failed (flags " + std::to_string(herr) + ") for op kind " +
+        return fail(CP_ESTATE, "transition table check failed (flags " + std::to_string(herr[0]) + ") for op kind " +
                                    std::to_string(op.kind) + " m=" + std::to_string(op.m) + " i=" +
                                    std::to_string(op.i));
     }

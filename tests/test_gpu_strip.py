@@ -146,6 +146,26 @@ def test_truncation_and_heights_against_modp_oracle(lattice):
                 assert got[k].tolist() == ref[p][H].tolist(), (H, p)
 
 
+# the eight largest primes below 2^31: the modular reduction's correction step
+# must not wrap around 2^32 when p is within a few thousand of 2^31
+TOP_PRIMES = [2147483647, 2147483629, 2147483587, 2147483579, 2147483563, 2147483549, 2147483543, 2147483497]
+
+
+@pytest.mark.parametrize("lattice", ["square", "triangular"])
+@pytest.mark.parametrize("n_primes", [8, 5])  # 16-byte rows (TMA gather) and 4-byte rows (register gather)
+def test_primes_just_below_2_31(lattice, n_primes):
+    primes = TOP_PRIMES[:n_primes]
+    L, D, heights = 11, 30, [6, 12]
+    with cp.Strip(lattice, L, primes, max_degree=D, max_rows=max(heights)) as s:
+        h = 1
+        for H in heights:
+            s.advance(H - h)
+            h = H
+            got = s.read()
+            for k, p in enumerate(primes):
+                assert got[k].tolist() == modp.ptilde_heights(lattice, L, [H], D, p)[H].tolist(), (H, p)
+
+
 @pytest.mark.parametrize("lattice", ["square", "triangular"])
 def test_transpose_symmetry(lattice):
     primes = gpu_util.seed_primes(4, seed=9)
