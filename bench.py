@@ -181,7 +181,7 @@ def tile_name(tile):
     rows, ring, passes = tile & 0xFFF, (tile >> 12) & 0xFF, (tile >> 20) & 7
     if rows <= 8:
         return "register gather kernel, %d rows/warp" % rows
-    return "TMA gather kernel, %d rows/block, %d KB ring, %d chunk(s)/thread" % (rows, ring or 48, passes or 1)
+    return "TMA gather kernel, %d rows/block, %d KB ring, %d chunk(s)/thread" % (rows, ring or 28, passes or 1)
 
 
 def plain_run(cp, torch, lattice, k, primes, stream):
@@ -568,6 +568,113 @@ def reference_arm(args):
     print(json.dumps(out))
 
 
+# ---------------------------------------------------------------- probe workload (one wide strip)
+
+def _probe_oracle_job(args):
+    L, rows, D, p = args
+    from oracle import modp
+    t = time.perf_counter()
+    modp.ptilde_heights("square", L, [rows + 1], D, p)
+    return time.perf_counter() - t
+
+
+def probe_arm(args):
+    """One square strip of width L (default 18: 3 210 246 intermediate states,
+    12.9 GB per vector at D = 62 and 16 primes): each step resets it to e_0,
+    advances `rows` rows (L per-site launches each) and reads P~ out.  The
+    per-site kernel runs far beyond the L2 here."""
+    import torch
+    import paper_1005_3609_gb300 as cp
+    pool = None
+    if not args.no_cpu_baseline:
+        pool = make_pool(min(16, os.cpu_count() or 1))  # spawn, before the first GPU call
+    L, D, P, rows = args.probe_L, args.probe_D, args.primes, args.probe_rows
+    primes = cp.select_primes(synthetic_inputs.prime_draws(0, 64), P)
+    stream = torch.cuda.Stream()
+    t_setup = time.perf_counter()
+    s = cp.Strip("square", L, primes, max_degree=D, max_rows=rows + 1, stream=stream)
+    setup_s = time.perf_counter() - t_setup
+    row_upd, row_bytes, ro_upd, ro_bytes = s.work()
+    out = torch.zeros(P * (D + 1), dtype=torch.int32, device="cuda")
+
+    def step():
+        s.reset()
+        s.advance(rows)
+        s.read_device(out.data_ptr(), out.numel())
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    upd_step = rows * row_upd + ro_upd
+    value = upd_step * args.steps / (ms / 1e3)
+    # roofline of the per-site gather: each row advance is L gather launches and nothing else
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * rows)]
+    s.reset()
+    for r in range(rows):
+        ev[2 * r].record(stream)
+        s.advance(1)
+        ev[2 * r + 1].record(stream)
+    torch.cuda.synchronize()
+    row_ms = sum(ev[2 * r].elapsed_time(ev[2 * r + 1]) for r in range(rows)) / rows
+    peaks = load_peaks()
+    peak = (peaks or {}).get("hbm_gbs") or 6800.0
+    achieved = row_bytes / (row_ms / 1e3) / 1e9
+    traffic = load_traffic("gather_kernel:probe:square:L%d:D%d:P%d" % (L, D, P))
+    # e2e through the C ABI: the read-out copied to host memory every step
+    host = None
+    f0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.reset()
+        s.advance(rows)
+        host = s.read()
+    e2e_ms = (time.perf_counter() - f0) * 1e3
+    n_states = s.n_states
+    s.close()
+    res = {"metric": "state-coeff updates/s (one wide strip, per-site gather)", "value": value, "unit": "updates/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+           "config": {"workload": "square strip width %d (%d NCNNN / %d intermediate states), %d primes, D=%d: "
+                                  "reset to e_0, %d rows, read-out" % (L, n_states[0], n_states[1], P, D, rows),
+                      "l2": "no flush: vectors %.1f GB each, > 100x L2" % (n_states[1] * (D + 1) * P * 4 / 1e9),
+                      "tables": "built before timing (%.1f s)" % setup_s, "tile": "strip default (TMA gather)",
+                      "updates_per_step": upd_step},
+           "e2e": {"value": upd_step * args.steps / (e2e_ms / 1e3), "unit": "updates/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 4 * P * (D + 1), "ms_per_step": e2e_ms / args.steps},
+           "gpu_launches": args.steps * (rows * L + (L - 1) + 1),
+           "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                        "frac": round(achieved / peak, 4),
+                        "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
+                        "algorithmic_bytes_per_launch": row_bytes / L, "avg_launch_ms": row_ms / L,
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s",
+                        "kernel": "per-site gather (row advance = %d launches)" % L}}
+    if clk:
+        res["clocks"] = clk
+    if pool is not None:
+        cL, cP = args.probe_cpu_L, min(P, min(16, os.cpu_count() or 1))
+        t = time.perf_counter()
+        pool.map(_probe_oracle_job, [(cL, rows, D, p) for p in primes[:cP]])
+        wall = time.perf_counter() - t
+        with cp.Strip("square", cL, primes[:1], max_degree=D, max_rows=rows + 1) as sc:
+            ru, _, ou, _ = sc.work()
+        cupd = (rows * ru + ou) * cP
+        res["cpu_baseline"] = {"value": cupd / wall, "unit": "updates/s", "cores": cP, "kind": "oracle",
+                               "sample": "plain-C mod-p oracle (hash-map TM), square width %d, %d rows, D=%d, %d "
+                                         "primes (one process each), %.1f s wall" % (cL, rows, D, cP, wall)}
+        pool.close()
+    print(json.dumps(res))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -582,7 +689,11 @@ def main():
     ap.add_argument("--cpu-widths", type=int, default=13, help="widths of the CPU-baseline sample")
     ap.add_argument("--ref-widths", type=int, default=11, help="widths of each reference-arm step")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "serve"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "serve", "probe"])
+    ap.add_argument("--probe-L", type=int, default=18, help="strip width of the probe workload")
+    ap.add_argument("--probe-D", type=int, default=62)
+    ap.add_argument("--probe-rows", type=int, default=4)
+    ap.add_argument("--probe-cpu-L", type=int, default=15, help="strip width of the probe's CPU-baseline sample")
     ap.add_argument("--serve-n", type=int, default=300, help="requests of the serving stream to run")
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-max-active", type=int, default=64)
@@ -592,6 +703,8 @@ def main():
         reference_arm(args)
     elif args.workload == "serve":
         serve_arm(args)
+    elif args.workload == "probe":
+        probe_arm(args)
     else:
         gpu_arm(args)
 

@@ -116,6 +116,14 @@ int cp_read_coeffs_device(cp_strip *s, uint32_t *out_dev, size_t out_len);
  * intermediate space, *degree = D, *height = current height. */
 int cp_strip_info(const cp_strip *s, uint64_t n_states[2], int *degree, int *height);
 
+/* Work of the strip's per-site factors, for throughput and roofline figures:
+ * work[0] = updates of one row advance (output words of T_1 .. T_L: sum of
+ * S_out (D+1) n_primes), work[1] = its algorithmic bytes (every factor reads
+ * its input vector and writes its output vector once, 4 (S_in + S_out)(D+1)
+ * n_primes, plus its CSR table, 4 (S_out + 1 + nnz)); work[2], work[3] = the
+ * same for one read-out (T_1^last .. T_{L-1}^last).  No GPU work. */
+int cp_strip_work(const cp_strip *s, uint64_t work[4]);
+
 /* Restart the strip at height 1 with the state vector e_0 (keeps its tables
  * and buffers).  Asynchronous on the strip's stream. */
 int cp_strip_reset(cp_strip *s);
@@ -183,7 +191,8 @@ typedef struct cp_sweep cp_sweep;
 
 /* tile: 0 = autotune; 1, 2, 4, 8 = register gather kernel, rows per warp;
  *       16, 32, 64, 128 = TMA gather kernel, rows per block, optionally plus
- *       (ring KB << 12) with ring KB in 32..192 (shared-memory ring size) and
+ *       (ring KB << 12) with ring KB in 16..192 (shared-memory ring size, 0 =
+ *       28 KB: seven blocks per SM) and
  *       (chunks per consumer thread << 20) with 1, 2, 4 or 8;
  * prime_groups: number of strips per width, dividing n_primes, or 0 = autotune.
  * cuda_stream must be a non-default stream (the program is graph-captured on it).

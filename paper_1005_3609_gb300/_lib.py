@@ -41,6 +41,7 @@ SIGNATURES = {
     "cp_strip_info": (ctypes.c_int, [vp, u64p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "cp_destroy": (None, [vp]),
     "cp_strip_reset": (ctypes.c_int, [vp]),
+    "cp_strip_work": (ctypes.c_int, [vp, u64p]),
     "cp_sweep_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, u32p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        vp, ctypes.POINTER(vp)]),
     "cp_sweep_run": (ctypes.c_int, [vp]),
@@ -201,6 +202,12 @@ class Strip:
 
     def reset(self):
         check("cp_strip_reset", load().cp_strip_reset(self._h))
+
+    def work(self):
+        """(row updates, row bytes, read-out updates, read-out bytes); see cp_strip_work."""
+        w = (ctypes.c_uint64 * 4)()
+        check("cp_strip_work", load().cp_strip_work(self._h, w))
+        return tuple(int(x) for x in w)
 
     def read_device(self, ptr, n_words):
         check("cp_read_coeffs_device", load().cp_read_coeffs_device(self._h, vp(ptr), n_words))

@@ -157,7 +157,7 @@ void append_gather_tasks(std::vector<GatherTask> *tasks, const SiteTable &tab, c
 // bits 20..23 = chunks per consumer thread, 1, 2, 4 or 8 (0: 1).  A batch whose
 // rows are not all 16-byte chunked (or too wide for the ring) uses the
 // register kernel.
-constexpr int kTmaRingKbDefault = 48;
+constexpr int kTmaRingKbDefault = 28;
 inline int make_tile(int rows, int ring_kb, int passes = 1) { return rows | (ring_kb << 12) | (passes << 20); }
 inline int tile_passes(int tile) { int p = (tile >> 20) & 15; return p ? p : 1; }
 inline int tile_ring_kb(int tile) { int r = (tile >> 12) & 0xFF; return r ? r : kTmaRingKbDefault; }

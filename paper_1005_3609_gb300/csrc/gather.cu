@@ -168,7 +168,8 @@ int effective_tile(const std::vector<GatherTask> &tasks, int items) {
     }
     int ring = (items >> 12) & 0xFF;
     if (!ring) ring = kTmaRingKbDefault;
-    ring = std::min(192, std::max(ring, (int)((8u * max_rb + 1023u) / 1024u)));  // >= 8 rows: one per group
+    // >= 16 KB and >= 4 rows: at least 4 slots per consumer group (G groups need rows <= 512 / G chunks)
+    ring = std::min(192, std::max(ring, std::max(16, (int)((4u * max_rb + 1023u) / 1024u))));
     return make_tile(items & 0xFFF, ring, passes);
 }
 

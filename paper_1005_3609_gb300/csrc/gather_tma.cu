@@ -2,8 +2,9 @@
 //
 // Same operation as gather_kernel: out[dst] = sum_e coef_e w^{shift_e} in[src_e]
 // (mod p).  A block owns a range of destination rows of one task.  Warp 0 is
-// the producer: it walks the block's CSR edges in order and, for each edge,
-// copies the part of the source row that survives the shift by w^{shift}
+// the producer: it walks the block's CSR edges in order, a few at a time with
+// one lane per edge, and for each edge copies the part of the source row that
+// survives the shift by w^{shift}
 // (degrees 0 .. D-shift) with one cp.async.bulk into the next slot of a
 // shared-memory ring, placed at degree offset `shift`, so that slot chunk c is
 // the source value that destination chunk c needs.  Each slot has a "full"
@@ -11,8 +12,8 @@
 // (completed when the eight consumer warps are done with it).  Warps 1..8
 // consume the slots in the same order: coef * slot[c] into signed 64-bit
 // accumulators, one reduction mod p per word, streaming stores of the
-// destination row.  The ring keeps up to ~190 KB of source rows in flight per
-// SM without using registers.
+// destination row.  With a 28 KB ring, seven blocks share an SM (seven
+// producers, ~196 KB of source rows in flight per SM) without using registers.
 //
 // Every mbarrier wait is bounded (kWaitCycles); on expiry the thread sets
 // *err and returns, and the producer first waits (bounded) for the copies it
@@ -29,6 +30,7 @@ constexpr int kTmaConsumers = 8;                      // consumer warps
 constexpr int kTmaThreads = 32 * (kTmaConsumers + 1);  // + producer warp
 constexpr int kTmaMaxSlots = 96;
 constexpr int kTmaMaxPasses = 8;                       // C <= 8 * 256 chunks
+constexpr uint32_t kIssueBatch = 2;                    // copies issued together by the producer warp
 constexpr long long kWaitCycles = 1ll << 31;           // ~1 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -87,7 +89,7 @@ __device__ __forceinline__ uint32_t reduce_s64_t(long long v, uint32_t p, float 
 // waits on).  More chunks per thread spread the per-edge work (barrier wait,
 // edge decode, release) over more data and put G rows in flight per block.
 template <int RPB, int PASSES>
-__global__ void __launch_bounds__(kTmaThreads, PASSES == 1 ? 4 : (PASSES == 2 ? 3 : (PASSES == 4 ? 2 : 1)))
+__global__ void __launch_bounds__(kTmaThreads, PASSES == 1 ? 7 : (PASSES == 2 ? 3 : (PASSES == 4 ? 2 : 1)))
     gather_tma_kernel(const GatherTask *__restrict__ tasks, int n_tasks, uint32_t ring_bytes, int *err) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ uint64_t full_bar[kTmaMaxSlots], empty_bar[kTmaMaxSlots];
@@ -155,50 +157,57 @@ __global__ void __launch_bounds__(kTmaThreads, PASSES == 1 ? 4 : (PASSES == 2 ? 
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (warp == 0) {
-        // ---------------- producer: one bulk copy per edge, in CSR order; the
-        // edge list is read 32 edges at a time with the next 32 prefetched, and
-        // the edge's row (hence sub-ring) is tracked as the index advances
+        // ---------------- producer: one bulk copy per edge, in CSR order, the
+        // copies of kIssueBatch consecutive edges issued together, one lane per
+        // edge (a batch holds at most nsub edges of any sub-ring, so its slots
+        // are distinct); a lane finds its edge's row by binary search of the
+        // block's row pointers, hence the edge's sub-ring and position in it.
+        // Issuing from several lanes keeps more copies in flight than one lane
+        // walking the edges could.
         const uint32_t e_begin = s_rp[0], e_end = s_rp[nrows];
+        const uint32_t B = min(kIssueBatch, nsub);
         bool ok = true;
-        uint32_t r = 0;  // row of the current edge (lane 0)
-        uint32_t qn = (e_begin + lane < e_end) ? __ldg(t.edges + e_begin + lane) : 0u;
-        for (uint32_t base = e_begin; base < e_end && ok; base += 32) {
-            const uint32_t q = qn;
-            qn = (base + 32 + lane < e_end) ? __ldg(t.edges + base + 32 + lane) : 0u;
-            const uint32_t n = min(32u, e_end - base);
-            for (uint32_t j = 0; j < n; ++j) {
-                const uint32_t qj = __shfl_sync(0xffffffffu, q, j);
-                if (lane == 0) {
-                    const uint32_t e = base + j;
-                    while (e >= s_rp[r + 1]) ++r;
-                    const uint32_t g = G > 1 ? r % G : 0u;
-                    const uint32_t cnt = (G > 1 ? s_gpos[r] + (e - s_rp[r]) : e - e_begin);
-                    const uint32_t qd = fast_div_u(cnt, nmagic);
-                    const uint32_t s = g * nsub + (cnt - qd * nsub), ph = qd & 1u;
-                    if (cnt >= nsub && !mbar_wait(smem_addr(&empty_bar[s]), ph ^ 1u, deadline)) {
-                        atomicOr(err, 2);
-                        ok = false;
+        uint32_t qn = (lane < B && e_begin + lane < e_end) ? __ldg(t.edges + e_begin + lane) : 0u;
+        for (uint32_t base = e_begin; base < e_end && ok; base += B) {
+            const uint32_t e = base + lane;
+            const uint32_t qj = qn;
+            qn = (lane < B && e + B < e_end) ? __ldg(t.edges + e + B) : 0u;  // next batch
+            bool lok = true;
+            if (lane < B && e < e_end) {
+                uint32_t g = 0, cnt = e - e_begin;
+                if (G > 1) {  // row of the edge: the last r with s_rp[r] <= e
+                    uint32_t lo = 0, hi = nrows - 1;
+                    while (lo < hi) {
+                        const uint32_t mid = (lo + hi + 1) >> 1;
+                        if (s_rp[mid] <= e) lo = mid; else hi = mid - 1;
                     }
-                    if (ok) {
-                        meta[s] = qj;
-                        const uint32_t back = ((qj >> t.src_bits) & 3u) * t.cpd;  // shift in chunks
-                        const uint32_t skip = back > t.c0 ? min(back - t.c0, t.cw) : 0u;
-                        const uint32_t bytes = (t.cw - skip) * 16u;
-                        const uint32_t fb = smem_addr(&full_bar[s]);
-                        if (bytes) {
-                            mbar_arrive_expect_tx(fb, bytes);
-                            bulk_copy_g2s(smem_addr(smem + (size_t)s * RB + skip * 16u),
-                                          in_bytes + (size_t)(qj & ((1u << t.src_bits) - 1u)) * src_row_bytes +
-                                              (size_t)(t.c0 + skip - back) * 16u,
-                                          bytes, fb);
-                        } else {
-                            mbar_arrive(fb);
-                        }
+                    g = lo & (G - 1);
+                    cnt = s_gpos[lo] + (e - s_rp[lo]);
+                }
+                const uint32_t qd = fast_div_u(cnt, nmagic);
+                const uint32_t s = g * nsub + (cnt - qd * nsub), ph = qd & 1u;
+                if (cnt >= nsub && !mbar_wait(smem_addr(&empty_bar[s]), ph ^ 1u, deadline)) {
+                    atomicOr(err, 2);
+                    lok = false;
+                }
+                if (lok) {
+                    meta[s] = qj;
+                    const uint32_t back = ((qj >> t.src_bits) & 3u) * t.cpd;  // shift in chunks
+                    const uint32_t skip = back > t.c0 ? min(back - t.c0, t.cw) : 0u;
+                    const uint32_t bytes = (t.cw - skip) * 16u;
+                    const uint32_t fb = smem_addr(&full_bar[s]);
+                    if (bytes) {
+                        mbar_arrive_expect_tx(fb, bytes);
+                        bulk_copy_g2s(smem_addr(smem + (size_t)s * RB + skip * 16u),
+                                      in_bytes + (size_t)(qj & ((1u << t.src_bits) - 1u)) * src_row_bytes +
+                                          (size_t)(t.c0 + skip - back) * 16u,
+                                      bytes, fb);
+                    } else {
+                        mbar_arrive(fb);
                     }
                 }
-                ok = __shfl_sync(0xffffffffu, ok, 0);
-                if (!ok) break;
             }
+            ok = __all_sync(0xffffffffu, lok);
         }
         // do not leave while own copies are in flight: wait for the last ones of every sub-ring
         if (lane == 0) {
@@ -280,7 +289,7 @@ __global__ void __launch_bounds__(kTmaThreads, PASSES == 1 ? 4 : (PASSES == 2 ? 
 // Ring sizes: one chunk pass uses ring_kb KB (several blocks per SM), more
 // passes the largest ring (one block per SM).
 constexpr uint32_t kTmaRingMax = 192 * 1024;
-constexpr uint32_t kTmaRingMin = 32 * 1024;
+constexpr uint32_t kTmaRingMin = 16 * 1024;
 
 bool tma_usable(const GatherTask &t) {
     if (!t.vec4 || t.cw > (uint32_t)(256 * kTmaMaxPasses)) return false;

@@ -289,6 +289,21 @@ extern "C" int cp_strip_info(const cp_strip *s, uint64_t n_states[2], int *degre
     return CP_OK;
 }
 
+extern "C" int cp_strip_work(const cp_strip *s, uint64_t work[4]) {
+    if (!s || !work) return fail(CP_EINVAL, "NULL argument");
+    const uint64_t row = (uint64_t)s->D1 * s->P;  // words per state
+    work[0] = work[1] = work[2] = work[3] = 0;
+    for (const SiteTable &t : s->tabs->row) {
+        work[0] += t.n_dst * row;
+        work[1] += 4 * (t.n_src + t.n_dst) * row + 4 * (t.n_dst + 1 + t.nnz);
+    }
+    for (const SiteTable &t : s->tabs->last) {
+        work[2] += t.n_dst * row;
+        work[3] += 4 * (t.n_src + t.n_dst) * row + 4 * (t.n_dst + 1 + t.nnz);
+    }
+    return CP_OK;
+}
+
 extern "C" int cp_strip_reset(cp_strip *s) {
     if (!s) return fail(CP_EINVAL, "strip is NULL");
     const size_t row_words = (size_t)s->D1 * s->P;
