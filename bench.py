@@ -177,6 +177,15 @@ def gather_source_sha():
     return h.hexdigest()[:16]
 
 
+def table_layout(cp, args):
+    """Apply --per-site-tables and describe the layout of the transfer-matrix tables."""
+    cp.set_factor_pairing(not args.per_site_tables)
+    if args.per_site_tables:
+        return "one table per site factor (r launches per row)"
+    return ("two-site tables: consecutive site factors composed in pairs (ceil(r/2) launches per row, the "
+            "intermediate vector never written); updates still counted per site factor")
+
+
 def tile_name(tile):
     rows, ring, passes = tile & 0xFFF, (tile >> 12) & 0xFF, (tile >> 20) & 7
     if rows <= 8:
@@ -247,6 +256,7 @@ def gpu_arm(args):
     primes = all_primes[lo:hi]
     stream = torch.cuda.Stream()
     t_setup = time.perf_counter()
+    layout = table_layout(cp, args)
     sw = cp.Sweep(lattice, k, primes, stream, tile=args.tile, prime_groups=args.groups)
     setup_s = time.perf_counter() - t_setup
     n = sw.n_terms
@@ -371,6 +381,7 @@ def gpu_arm(args):
                           "l2": "no flush: working set > L2 (width-16 vectors %.2f GB each)" %
                                 (strip_bytes_max(lattice, k, n, P) / 1e9),
                           "tables": "built once per (lattice, width) before timing (%.2f s incl. autotune)" % setup_s,
+                          "factor_tables": layout,
                           "tile": tile_name(sw.tile), "prime_groups": sw.prime_groups,
                           "updates_per_step": sw.updates_per_run, "algorithmic_bytes_per_step": sw.bytes_per_run},
                "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": h2d,
@@ -592,9 +603,11 @@ def probe_arm(args):
     primes = cp.select_primes(synthetic_inputs.prime_draws(0, 64), P)
     stream = torch.cuda.Stream()
     t_setup = time.perf_counter()
+    layout = table_layout(cp, args)
     s = cp.Strip("square", L, primes, max_degree=D, max_rows=rows + 1, stream=stream)
     setup_s = time.perf_counter() - t_setup
     row_upd, row_bytes, ro_upd, ro_bytes = s.work()
+    len_row = L if args.per_site_tables else (L + 1) // 2  # gather launches per row
     out = torch.zeros(P * (D + 1), dtype=torch.int32, device="cuda")
 
     def step():
@@ -648,16 +661,17 @@ def probe_arm(args):
                                   "reset to e_0, %d rows, read-out" % (L, n_states[0], n_states[1], P, D, rows),
                       "l2": "no flush: vectors %.1f GB each, > 100x L2" % (n_states[1] * (D + 1) * P * 4 / 1e9),
                       "tables": "built before timing (%.1f s)" % setup_s, "tile": "strip default (TMA gather)",
+                      "factor_tables": layout,
                       "updates_per_step": upd_step},
            "e2e": {"value": upd_step * args.steps / (e2e_ms / 1e3), "unit": "updates/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 4 * P * (D + 1), "ms_per_step": e2e_ms / args.steps},
-           "gpu_launches": args.steps * (rows * L + (L - 1) + 1),
+           "gpu_launches": args.steps * (rows * len_row + (L - 1 if args.per_site_tables else L // 2) + 1),
            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(achieved / peak, 4),
                         "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
-                        "algorithmic_bytes_per_launch": row_bytes / L, "avg_launch_ms": row_ms / L,
+                        "algorithmic_bytes_per_launch": row_bytes / len_row, "avg_launch_ms": row_ms / len_row,
                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s",
-                        "kernel": "per-site gather (row advance = %d launches)" % L}}
+                        "kernel": "TMA gather (row advance = %d launches)" % len_row}}
     if clk:
         res["clocks"] = clk
     if pool is not None:
@@ -698,6 +712,8 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-max-active", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--per-site-tables", action="store_true",
+                    help="one table per site factor instead of two-site tables (same results)")
     args = ap.parse_args()
     if args.impl == "reference":
         reference_arm(args)

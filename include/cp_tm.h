@@ -131,6 +131,20 @@ int cp_strip_reset(cp_strip *s);
 void cp_destroy(cp_strip *s);
 
 /*
+ * cp_set_factor_pairing -- how the chromatic tables built from now on are laid
+ * out (strips, sweeps and server jobs created afterwards; tables already built
+ * stay cached under their own layout).  on = 1 (the default): one two-site
+ * table per consecutive pair of per-site factors, T_2 T_1, T_4 T_3, ... of the
+ * row and of the read-out chain (an odd one out stays single), so a row of L
+ * sites takes ceil(L/2) gather launches and the intermediate vector of each
+ * pair is never written: the same matrix product as the factorisation of
+ * Sec. 3.2-3.3 with half the vector traffic.  on = 0: one table per factor, as
+ * in the paper.  Results are identical either way.  Returns the previous
+ * setting.  Not thread-safe against concurrent strip creation.
+ */
+int cp_set_factor_pairing(int on);
+
+/*
  * cp_crt -- Chinese remaindering (Sec. 3.5): for each of n_coeffs
  * coefficients, residues_host[k*n_coeffs + j] modulo primes_host[k] ->
  * the integer in (-prod/2, prod/2], written as limbs_per_coeff little-endian

@@ -5,4 +5,4 @@ include/cp_tm.h); this package is its Python binding.  Importing it does not
 load the library; the first call does, and raises if it is not built.
 """
 from ._lib import (CP_MAX_L, CP_MAX_PRIMES, CPError, Server, Strip, Sweep, crt, crt_static, debug_check_space,  # noqa: F401
-                   debug_enumerate_space, load, select_primes)
+                   debug_enumerate_space, load, select_primes, set_factor_pairing)

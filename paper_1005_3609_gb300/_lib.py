@@ -42,6 +42,7 @@ SIGNATURES = {
     "cp_destroy": (None, [vp]),
     "cp_strip_reset": (ctypes.c_int, [vp]),
     "cp_strip_work": (ctypes.c_int, [vp, u64p]),
+    "cp_set_factor_pairing": (ctypes.c_int, [ctypes.c_int]),
     "cp_sweep_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, u32p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                        vp, ctypes.POINTER(vp)]),
     "cp_sweep_run": (ctypes.c_int, [vp]),
@@ -228,6 +229,12 @@ class Strip:
 
     def __exit__(self, *a):
         self.close()
+
+
+def set_factor_pairing(on):
+    """Two-site tables (True, the default) or one table per site factor for tables
+    built from now on (cp_set_factor_pairing); returns the previous setting."""
+    return bool(load().cp_set_factor_pairing(1 if on else 0))
 
 
 def debug_check_space(kind, m, e=0):

@@ -76,6 +76,10 @@ struct OpDesc {
     Space in, out;
     int32_t v;         // Potts coupling (OP_POTTS_*)
     int32_t src_bits;  // edge format of the table
+    int32_t fused;     // 1: two-site table, factor (kind_b, i_b) applied after (kind, i)
+    int32_t kind_b;
+    int32_t i_b;
+    int32_t pad2;
 };
 
 // Packed CSR edge: src (src_bits) | shift << src_bits (2 bits) | coef << (src_bits + 2)
@@ -95,16 +99,20 @@ inline int potts_src_bits(uint64_t n_states) {
 struct SiteTable {
     OpDesc op;
     uint64_t n_src = 0, n_dst = 0, nnz = 0;
+    uint64_t n_site_out = 0;  // output states of the per-site factors it stands for (n_dst, or mid + n_dst)
     uint32_t *row_ptr = nullptr;  // [n_dst + 1]
     uint32_t *edges = nullptr;    // [nnz]
 };
 
 // All tables of one (lattice, L) on one device; shared between strips.
 struct TableSet {
-    int device = 0, lattice = 0, L = 0, potts = 0, v = -1, src_bits = (int)kSrcBits;
+    int device = 0, lattice = 0, L = 0, potts = 0, v = -1, src_bits = (int)kSrcBits, paired = 0;
     uint64_t S_b = 0, S_max = 0;
-    std::vector<SiteTable> row;   // T_1..T_L
-    std::vector<SiteTable> last;  // T_1^last..T_{L-1}^last (identity for L = 1)
+    // T_1..T_L and T_1^last..T_{L-1}^last (identity for L = 1), one table per
+    // factor, or (paired) one two-site table per consecutive pair of factors
+    // (T_2 T_1, T_4 T_3, ...; an odd one out stays single)
+    std::vector<SiteTable> row;
+    std::vector<SiteTable> last;
     std::vector<uint32_t *> x_prefix;  // square lattice: prefix table of X_e, e = 0..L-2
     size_t bytes = 0;
     ~TableSet();
@@ -117,8 +125,12 @@ int device_rank_tables(const RankTables **out_dev, RankTables *host_copy);
 int build_x_prefix(int m, int e, cudaStream_t st, uint32_t **out);
 
 // Build or fetch from the cache the tables of (lattice, L) on the current device
-// (chromatic polynomial: the projected factorisation of Sec. 3.2-3.3).
+// (chromatic polynomial: the projected factorisation of Sec. 3.2-3.3), paired
+// or not according to factor_pairing().
 int get_tables(int lattice, int L, cudaStream_t stream, std::shared_ptr<TableSet> *out);
+// Library-wide choice for tables built from now on: 1 = two-site tables (default), 0 = one per factor.
+int factor_pairing();
+int set_factor_pairing(int on);
 // Tables of the any-v Potts transfer matrix T_i = V_i H_{i,i+1} (square) or
 // V_i H_{i-1,i} H_{i,i+1} (triangular) on non-crossing partitions.
 int get_potts_tables(int lattice, int L, int v, cudaStream_t stream, std::shared_ptr<TableSet> *out);

@@ -135,7 +135,8 @@ struct cp_server {
 };
 
 static size_t request_bytes(const TableSet &ts, int L, size_t RB) {
-    const uint64_t sA = L >= 2 ? ts.last[0].n_dst : 1, sB = L >= 3 ? ts.last[1].n_dst : 1;
+    (void)L;
+    const uint64_t sA = ts.last[0].n_dst, sB = ts.last.size() >= 2 ? ts.last[1].n_dst : 1;
     auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
     return 2 * al(ts.S_max * RB) + al(sA * RB) + al(sB * RB) + 2 * al(RB) + al(4 * CP_MAX_PRIMES);
 }
@@ -189,7 +190,7 @@ static int admit(cp_server *sv, Job *j, bool *fits) {
         p += (b + 255) & ~(size_t)255;
         return reinterpret_cast<uint32_t *>(q);
     };
-    const uint64_t sA = j->L >= 2 ? ts.last[0].n_dst : 1, sB = j->L >= 3 ? ts.last[1].n_dst : 1;
+    const uint64_t sA = ts.last[0].n_dst, sB = ts.last.size() >= 2 ? ts.last[1].n_dst : 1;
     j->vec[0] = take(ts.S_max * RB);
     j->vec[1] = take(ts.S_max * RB);
     j->scratch[0] = take(sA * RB);
@@ -203,19 +204,20 @@ static int admit(cp_server *sv, Job *j, bool *fits) {
                                                  1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
     CP_CUDA_TRY(cudaMemcpyAsync(j->vec[0], ones, 4 * j->P, cudaMemcpyHostToDevice, sv->stream));
     j->op = 0;
-    j->n_ops = (j->N - 1) * j->L + (int)ts.last.size();
+    j->n_ops = (j->N - 1) * (int)ts.row.size() + (int)ts.last.size();
     return CP_OK;
 }
 
 // Task of job j's next factor; returns true if this was the last one.
 static bool next_tasks(Job *j, std::vector<GatherTask> *tasks, uint64_t *upd) {
     const TableSet &ts = *j->tabs;
-    const int main_ops = (j->N - 1) * j->L;
+    const int nrow = (int)ts.row.size();
+    const int main_ops = (j->N - 1) * nrow;
     const SiteTable *tab;
     const uint32_t *in;
     uint32_t *out;
     if (j->op < main_ops) {
-        const int i = j->op % j->L;
+        const int i = j->op % nrow;
         tab = &ts.row[i];
         in = j->vec[j->op & 1];
         out = j->vec[(j->op & 1) ^ 1];
@@ -229,7 +231,7 @@ static bool next_tasks(Job *j, std::vector<GatherTask> *tasks, uint64_t *upd) {
     // updates count the requested primes only (padding lanes are not work asked for)
     int real = 0;
     for (auto &m : j->members) real += m.first->P;
-    *upd += tab->n_dst * (uint64_t)j->D1 * real;
+    *upd += tab->n_site_out * (uint64_t)j->D1 * real;
     return ++j->op == j->n_ops;
 }
 

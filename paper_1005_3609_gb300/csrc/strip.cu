@@ -158,7 +158,7 @@ static int make_strip(std::shared_ptr<TableSet> tabs, int lattice, int L, const 
     for (int k = 0; k < 2; ++k)
         if ((rc = dev_alloc((void **)&s->vec[k], ts.S_max * row_words * 4))) return rc;
     // read-out scratch: T_1^last writes cnt[L-1] rows, T_2^last cnt[L-2], ...
-    uint64_t sA = L >= 2 ? ts.last[0].n_dst : 1, sB = L >= 3 ? ts.last[1].n_dst : 1;
+    uint64_t sA = ts.last[0].n_dst, sB = ts.last.size() >= 2 ? ts.last[1].n_dst : 1;
     if ((rc = dev_alloc((void **)&s->scratch[0], sA * row_words * 4))) return rc;
     if ((rc = dev_alloc((void **)&s->scratch[1], sB * row_words * 4))) return rc;
     if ((rc = dev_alloc((void **)&s->row_out, row_words * 4))) return rc;
@@ -172,7 +172,7 @@ static int make_strip(std::shared_ptr<TableSet> tabs, int lattice, int L, const 
     std::vector<GatherTask> all;
     for (int b = 0; b < 2; ++b) {
         int cur = b;
-        for (int i = 0; i < L; ++i) {
+        for (size_t i = 0; i < ts.row.size(); ++i) {
             std::vector<GatherTask> l;
             append_gather_tasks(&l, ts.row[i], s->vec[cur], s->vec[cur ^ 1], s->primes_dev, s->D1, s->P);
             s->row_tasks[b].push_back(l);
@@ -237,12 +237,13 @@ extern "C" int cp_advance_rows(cp_strip *s, int n_rows) {
     if (n_rows < 0 || (long long)s->height + n_rows > s->max_rows) return fail(CP_EINVAL, "height would exceed max_rows");
     for (int r = 0; r < n_rows; ++r) {
         const int b = s->cur;
-        for (int i = 0; i < s->L; ++i) {
+        const int nrow = (int)s->row_tasks[b].size();
+        for (int i = 0; i < nrow; ++i) {
             int rc = launch_gather(s->row_dev[b][i], (int)s->row_tasks[b][i].size(),
                                    list_blocks(s->row_tasks[b][i], s->tile), s->tile, s->stream);
             if (rc) return rc;
         }
-        s->cur = (b + s->L) & 1;
+        s->cur = (b + nrow) & 1;
         s->height += 1;
     }
     return CP_OK;
@@ -294,11 +295,11 @@ extern "C" int cp_strip_work(const cp_strip *s, uint64_t work[4]) {
     const uint64_t row = (uint64_t)s->D1 * s->P;  // words per state
     work[0] = work[1] = work[2] = work[3] = 0;
     for (const SiteTable &t : s->tabs->row) {
-        work[0] += t.n_dst * row;
+        work[0] += t.n_site_out * row;
         work[1] += 4 * (t.n_src + t.n_dst) * row + 4 * (t.n_dst + 1 + t.nnz);
     }
     for (const SiteTable &t : s->tabs->last) {
-        work[2] += t.n_dst * row;
+        work[2] += t.n_site_out * row;
         work[3] += 4 * (t.n_src + t.n_dst) * row + 4 * (t.n_dst + 1 + t.nnz);
     }
     return CP_OK;
@@ -326,3 +327,5 @@ namespace cp {
 void clear_table_cache();
 }
 extern "C" void cp_clear_table_cache(void) { cp::clear_table_cache(); }
+
+extern "C" int cp_set_factor_pairing(int on) { return cp::set_factor_pairing(on); }

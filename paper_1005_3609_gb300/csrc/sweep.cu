@@ -91,7 +91,7 @@ static int rect_index(const cp_sweep *sw, int r, int s) {
 // Accumulate the algorithmic work of one factor: output words, and bytes =
 // 4 (S_in + S_out) (D+1) Pg + CSR index bytes.
 static void count_work(cp_sweep *sw, const SiteTable &t, int Pg) {
-    sw->updates += t.n_dst * (uint64_t)sw->D1 * Pg;
+    sw->updates += t.n_site_out * (uint64_t)sw->D1 * Pg;
     sw->bytes += 4ull * (t.n_src + t.n_dst) * sw->D1 * Pg + 4ull * (t.n_dst + 1 + t.nnz);
 }
 
@@ -119,7 +119,7 @@ static int build_strips(cp_sweep *sw) {
             SweepStrip &sp = sw->strips.back();
             for (int b = 0; b < 2; ++b)
                 if ((rc = dev_alloc((void **)&sp.vec[b], ts.S_max * row_words * 4))) return rc;
-            uint64_t sA = r >= 2 ? ts.last[0].n_dst : 1, sB = r >= 3 ? ts.last[1].n_dst : 1;
+            uint64_t sA = ts.last[0].n_dst, sB = ts.last.size() >= 2 ? ts.last[1].n_dst : 1;
             if ((rc = dev_alloc((void **)&sp.scratch[0], sA * row_words * 4))) return rc;
             if ((rc = dev_alloc((void **)&sp.scratch[1], sB * row_words * 4))) return rc;
         }
@@ -158,16 +158,17 @@ static int build_program(cp_sweep *sw, int tile) {
         const int r = st.r;
         const uint32_t *pr = sw->primes_dev + st.group * Pg;
         const int smax = st.heights.back();
-        // main lane: rows 1..smax-1, factor i of row h is step (h-1)*r + i
+        const int nf = (int)ts.row.size();  // launches per row (factors, or pairs of factors)
+        // main lane: rows 1..smax-1, launch i of row h is step (h-1)*nf + i
         for (int row = 0; row < smax - 1; ++row)
-            for (int i = 0; i < r; ++i) {
-                const size_t t = (size_t)row * r + i;
+            for (int i = 0; i < nf; ++i) {
+                const size_t t = (size_t)row * nf + i;
                 append_gather_tasks(&at(t), ts.row[i], st.vec[t & 1], st.vec[(t & 1) ^ 1], pr, sw->D1, Pg);
                 count_work(sw, ts.row[i], Pg);
             }
         // read-out lanes
         for (int h : st.heights) {
-            const size_t t0 = (size_t)(h - 1) * r;
+            const size_t t0 = (size_t)(h - 1) * nf;
             const uint32_t *src = st.vec[t0 & 1];
             uint32_t *slot = sw->ptilde_dev + ((size_t)st.group * n_rects + rect_index(sw, r, h)) * row_words;
             int sc = 0;

@@ -68,7 +68,8 @@ struct Term {
     int32_t shift;
 };
 
-constexpr int kMaxTerms = 8;
+constexpr int kMaxTerms = 8;   // terms of one factor applied to one partition
+constexpr int kMaxFused = 64;  // terms of a two-site table before merging
 
 // H_{a,b} = 1 - J_{a,b} at v = -1: a term with a ~ b is killed (H s = s - s), otherwise
 // it splits into itself and the joined partition with -w.
@@ -194,9 +195,31 @@ __device__ int factor_terms(const OpDesc &op, const Labels &s, Term *t) {
     return n;
 }
 
+// Terms of a two-site table: the second factor applied to every term of the first.
+__device__ int fused_terms(const OpDesc &op, const Labels &s, Term *out) {
+    Term a[kMaxTerms];
+    const int na = factor_terms(op, s, a);
+    OpDesc ob = op;
+    ob.kind = op.kind_b;
+    ob.i = op.i_b;
+    int n = 0;
+    for (int j = 0; j < na; ++j) {
+        Term b[kMaxTerms];
+        const int nb = factor_terms(ob, a[j].s, b);
+        for (int q = 0; q < nb; ++q) {
+            out[n].s = b[q].s;
+            out[n].coef = a[j].coef * b[q].coef;
+            out[n].shift = a[j].shift + b[q].shift;
+            ++n;
+        }
+    }
+    return n;
+}
+
 // One thread per source state.  slot_dst[src*K + t] = destination rank or ~0u,
 // slot_edge[...] = packed edge.  err bits: 1 bad rank / membership, 2 too many
 // terms, 4 coefficient out of range, 8 unrank/rank mismatch of the source.
+template <int NT>
 __global__ void build_terms_kernel(OpDesc op, const RankTables *Tg, uint32_t *slot_dst, uint32_t *slot_edge,
                                    int K, int *err) {
     __shared__ RankTables T;
@@ -207,9 +230,9 @@ __global__ void build_terms_kernel(OpDesc op, const RankTables *Tg, uint32_t *sl
     space_unrank(src, op.in, s, T);
     int bad = 0;
     if (!space_contains(s, op.in) || space_rank(s, op.in, T) != src) bad |= 8;
-    Term t[kMaxTerms];
-    int n = factor_terms(op, s, t);
-    uint32_t dst[kMaxTerms];
+    Term t[NT];
+    int n = op.fused ? fused_terms(op, s, t) : factor_terms(op, s, t);
+    uint32_t dst[NT];
     for (int j = 0; j < n; ++j) {
         if (!space_contains(t[j].s, op.out)) { bad |= 1; dst[j] = ~0u; continue; }
         uint64_t r = space_rank(t[j].s, op.out, T);
@@ -426,6 +449,7 @@ static int build_table(const OpDesc &op, const RankTables *T_dev, cudaStream_t s
     tab->op = op;
     tab->n_src = op.in.size;
     tab->n_dst = op.out.size;
+    tab->n_site_out = op.out.size;
     if (op.in.size > ((1ull << op.src_bits) - 1) || op.out.size >= 0xFFFFFFFFull)
         return fail(CP_EINVAL, "state space too large for the edge format");
     const int K = op.max_terms;
@@ -457,7 +481,12 @@ static int build_table(const OpDesc &op, const RankTables *T_dev, cudaStream_t s
     cudaMemsetAsync(csum, 0, op.out.size * 4, st);
     cudaMemsetAsync(err, 0, 2 * sizeof(int), st);
     const int bt = 128;
-    build_terms_kernel<<<(unsigned)((op.in.size + bt - 1) / bt), bt, 0, st>>>(op, T_dev, slot_dst, slot_edge, K, err);
+    if (op.fused)
+        build_terms_kernel<kMaxFused><<<(unsigned)((op.in.size + bt - 1) / bt), bt, 0, st>>>(op, T_dev, slot_dst,
+                                                                                            slot_edge, K, err);
+    else
+        build_terms_kernel<kMaxTerms><<<(unsigned)((op.in.size + bt - 1) / bt), bt, 0, st>>>(op, T_dev, slot_dst,
+                                                                                            slot_edge, K, err);
     count_kernel<<<1216, 256, 0, st>>>(slot_dst, slot_edge, n_slots, op.src_bits, cnt, csum);
     max_count_kernel<<<608, 256, 0, st>>>(csum, op.out.size, err + 1);
     cudaError_t e = cudaGetLastError();
@@ -531,7 +560,7 @@ static int identity_table(int m, SiteTable *tab) {
     op.in = Space{SPACE_B, m, 0, 0, 1, nullptr};
     op.out = op.in;
     tab->op = op;
-    tab->n_src = tab->n_dst = tab->nnz = 1;
+    tab->n_src = tab->n_dst = tab->nnz = tab->n_site_out = 1;
     int rc = dev_alloc((void **)&tab->row_ptr, 8);
     if (rc) return rc;
     if ((rc = dev_alloc((void **)&tab->edges, 4))) return rc;
@@ -541,7 +570,39 @@ static int identity_table(int m, SiteTable *tab) {
     return CP_OK;
 }
 
-static int build_tableset(int lattice, int L, cudaStream_t st, std::shared_ptr<TableSet> *out) {
+// Tables of a chain of per-site factors: one per factor, or (paired) one
+// two-site table per consecutive pair, the second factor composed after the
+// first on every term (an odd one out stays single).  Two chromatic factors
+// compose to shifts of at most 3 and coefficients of magnitude at most 5
+// (square) or 10 (triangular), so the edges keep a 2-bit shift and take 26 or
+// 25 source bits; the build checks both bounds.
+static int build_chain(const std::vector<OpDesc> &ops, int paired, int lattice, const RankTables *T_dev,
+                       cudaStream_t st, TableSet *ts, std::vector<SiteTable> *out) {
+    int rc;
+    for (size_t i = 0; i < ops.size();) {
+        SiteTable tab;
+        if (paired && i + 1 < ops.size()) {
+            OpDesc f = ops[i];
+            f.fused = 1;
+            f.kind_b = ops[i + 1].kind;
+            f.i_b = ops[i + 1].i;
+            f.out = ops[i + 1].out;
+            f.max_terms = ops[i].kind == OP_LAST ? 4 : (lattice == CP_SQUARE ? 16 : 24);
+            f.src_bits = lattice == CP_SQUARE ? 26 : 25;
+            if ((rc = build_table(f, T_dev, st, &tab))) return rc;
+            tab.n_site_out = ops[i].out.size + ops[i + 1].out.size;
+            i += 2;
+        } else {
+            if ((rc = build_table(ops[i], T_dev, st, &tab))) return rc;
+            i += 1;
+        }
+        ts->bytes += (tab.n_dst + 1 + tab.nnz) * 4;
+        out->push_back(tab);
+    }
+    return CP_OK;
+}
+
+static int build_tableset(int lattice, int L, int paired, cudaStream_t st, std::shared_ptr<TableSet> *out) {
     const RankTables *T_dev = nullptr;
     RankTables T;
     int rc = device_rank_tables(&T_dev, &T);
@@ -550,6 +611,7 @@ static int build_tableset(int lattice, int L, cudaStream_t st, std::shared_ptr<T
     cudaGetDevice(&ts->device);
     ts->lattice = lattice;
     ts->L = L;
+    ts->paired = paired;
     const uint64_t Sb = T.cnt[L];
     const uint64_t Sx = L >= 2 ? T.cnt[L] + T.cnt[L - 1] : Sb;
     ts->S_b = Sb;
@@ -562,6 +624,7 @@ static int build_tableset(int lattice, int L, cudaStream_t st, std::shared_ptr<T
             ts->bytes += (Sb + 1) * 4;
         }
     }
+    std::vector<OpDesc> row_ops, last_ops;
     for (int i = 0; i < L; ++i) {
         OpDesc op{};
         op.m = L;
@@ -578,30 +641,26 @@ static int build_tableset(int lattice, int L, cudaStream_t st, std::shared_ptr<T
             op.in = Space{SPACE_B, L, 0, 0, Sb, nullptr};
             op.out = op.in;
         }
-        SiteTable tab;
-        if ((rc = build_table(op, T_dev, st, &tab))) return rc;
-        ts->bytes += (tab.n_dst + 1 + tab.nnz) * 4;
-        ts->row.push_back(tab);
+        row_ops.push_back(op);
     }
+    for (int i = 0; i + 1 < L; ++i) {  // T_L^last = D_L is the identity on e_0
+        OpDesc op{};
+        op.kind = OP_LAST;
+        op.m = L;
+        op.i = i;
+        op.src_bits = (int)kSrcBits;
+        op.max_terms = 2;
+        op.in = Space{SPACE_B, L, 0, 0, T.cnt[L - i], nullptr};
+        op.out = Space{SPACE_B, L, 0, 0, T.cnt[L - i - 1], nullptr};
+        last_ops.push_back(op);
+    }
+    if ((rc = build_chain(row_ops, paired, lattice, T_dev, st, ts.get(), &ts->row))) return rc;
     if (L == 1) {
         SiteTable tab;
         if ((rc = identity_table(1, &tab))) return rc;
         ts->last.push_back(tab);
-    } else {
-        for (int i = 0; i + 1 < L; ++i) {  // T_L^last = D_L is the identity on e_0
-            OpDesc op{};
-            op.kind = OP_LAST;
-            op.m = L;
-            op.i = i;
-            op.src_bits = (int)kSrcBits;
-            op.max_terms = 2;
-            op.in = Space{SPACE_B, L, 0, 0, T.cnt[L - i], nullptr};
-            op.out = Space{SPACE_B, L, 0, 0, T.cnt[L - i - 1], nullptr};
-            SiteTable tab;
-            if ((rc = build_table(op, T_dev, st, &tab))) return rc;
-            ts->bytes += (tab.n_dst + 1 + tab.nnz) * 4;
-            ts->last.push_back(tab);
-        }
+    } else if ((rc = build_chain(last_ops, paired, lattice, T_dev, st, ts.get(), &ts->last))) {
+        return rc;
     }
     *out = ts;
     return CP_OK;
@@ -663,7 +722,20 @@ static int build_potts_tableset(int lattice, int L, int v, cudaStream_t st, std:
 }
 
 static std::mutex g_cache_mu;
-static std::map<std::pair<int, int>, std::shared_ptr<TableSet>> g_cache[64];  // per device
+static std::map<std::tuple<int, int, int>, std::shared_ptr<TableSet>> g_cache[64];  // per device
+static int g_pairing = 1;
+
+int factor_pairing() {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    return g_pairing;
+}
+
+int set_factor_pairing(int on) {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    const int old = g_pairing;
+    g_pairing = on ? 1 : 0;
+    return old;
+}
 static std::map<std::tuple<int, int, int>, std::shared_ptr<TableSet>> g_potts_cache[64];
 
 int get_tables(int lattice, int L, cudaStream_t st, std::shared_ptr<TableSet> *out) {
@@ -671,14 +743,14 @@ int get_tables(int lattice, int L, cudaStream_t st, std::shared_ptr<TableSet> *o
     CP_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(CP_EINVAL, "device index");
     std::lock_guard<std::mutex> lk(g_cache_mu);
-    auto key = std::make_pair(lattice, L);
+    auto key = std::make_tuple(lattice, L, g_pairing);
     auto it = g_cache[dev].find(key);
     if (it != g_cache[dev].end()) {
         *out = it->second;
         return CP_OK;
     }
     std::shared_ptr<TableSet> ts;
-    int rc = build_tableset(lattice, L, st, &ts);
+    int rc = build_tableset(lattice, L, g_pairing, st, &ts);
     if (rc) return rc;
     g_cache[dev][key] = ts;
     *out = ts;
