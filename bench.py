@@ -179,11 +179,12 @@ def gather_source_sha():
 
 def table_layout(cp, args):
     """Apply --per-site-tables and describe the layout of the transfer-matrix tables."""
-    cp.set_factor_pairing(not args.per_site_tables)
+    cp.set_factor_pairing(0 if args.per_site_tables else 1)
     if args.per_site_tables:
         return "one table per site factor (r launches per row)"
-    return ("two-site tables: consecutive site factors composed in pairs (ceil(r/2) launches per row, the "
-            "intermediate vector never written); updates still counted per site factor")
+    return ("square lattice, rows >= 3 KB: two-site tables, consecutive site factors composed in pairs (ceil(r/2) "
+            "launches per row, the intermediate vector never written); otherwise one table per site factor; "
+            "updates counted per site factor either way")
 
 
 def tile_name(tile):
@@ -353,18 +354,23 @@ def gpu_arm(args):
     gather_ms, n_gather, pass_ms = sw.profile()
     peaks = load_peaks()
     peak = peaks.get("hbm_gbs") if peaks else None
-    achieved = sw.bytes_per_run / (gather_ms / 1e3) / 1e9
-    traffic = load_traffic("gather_kernel:%s:k%d:P%d" % (lattice, k, P))
+    peak = peak or 6800.0
+    # algorithmic bytes as defined per update (every per-site factor reads its input and writes its
+    # output vector once); with two-site tables the launched tables need fewer (reported beside)
+    achieved = sw.site_bytes_per_run / (gather_ms / 1e3) / 1e9
+    traffic = load_traffic("gather_kernel:%s:k%d:P%d:%s" % (lattice, k, P, "site" if args.per_site_tables else "auto"))
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4) if peak else None,
+                "frac": round(achieved / peak, 4),
                 "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
-                "algorithmic_bytes_per_launch": sw.bytes_per_run / n_gather,
+                "algorithmic_bytes_per_launch": sw.site_bytes_per_run / n_gather,
                 "avg_launch_ms": gather_ms / n_gather,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peak else "fallback 6800 GB/s",
-                "kernel": "batched per-site gather: %s" % tile_name(sw.tile)}
-    if not peak:
-        roofline["peak"] = 6800.0
-        roofline["frac"] = round(achieved / 6800.0, 4)
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s",
+                "kernel": "batched gather: %s" % tile_name(sw.tile)}
+    if sw.bytes_per_run != sw.site_bytes_per_run:
+        own = sw.bytes_per_run / (gather_ms / 1e3) / 1e9
+        roofline["tables_own_bytes"] = {
+            "bytes_per_launch": sw.bytes_per_run / n_gather, "achieved": round(own, 1), "frac": round(own / peak, 4),
+            "note": "bytes the two-site tables themselves need (input, output, CSR; no intermediate vector)"}
 
     out = None
     if rank == 0:
@@ -383,12 +389,14 @@ def gpu_arm(args):
                           "tables": "built once per (lattice, width) before timing (%.2f s incl. autotune)" % setup_s,
                           "factor_tables": layout,
                           "tile": tile_name(sw.tile), "prime_groups": sw.prime_groups,
-                          "updates_per_step": sw.updates_per_run, "algorithmic_bytes_per_step": sw.bytes_per_run},
+                          "updates_per_step": sw.updates_per_run,
+                          "algorithmic_bytes_per_step": sw.site_bytes_per_run,
+                          "table_bytes_per_step": sw.bytes_per_run},
                "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
                "gpu_launches": args.steps * (sw.launches_per_run + 3),
                "roofline": roofline,
-               "hbm_gbs_algorithmic": sw.bytes_per_run * args.steps / (ms / 1e3) / 1e9}
+               "hbm_gbs_algorithmic": sw.site_bytes_per_run * args.steps / (ms / 1e3) / 1e9}
         if clk:
             out["clocks"] = clk
         if lattice == "square" and k in (33, 41):
@@ -606,8 +614,9 @@ def probe_arm(args):
     layout = table_layout(cp, args)
     s = cp.Strip("square", L, primes, max_degree=D, max_rows=rows + 1, stream=stream)
     setup_s = time.perf_counter() - t_setup
-    row_upd, row_bytes, ro_upd, ro_bytes = s.work()
-    len_row = L if args.per_site_tables else (L + 1) // 2  # gather launches per row
+    row_upd, row_own, ro_upd, ro_own, row_bytes, ro_bytes = s.work()
+    paired = row_own < row_bytes
+    len_row = (L + 1) // 2 if paired else L  # gather launches per row
     out = torch.zeros(P * (D + 1), dtype=torch.int32, device="cuda")
 
     def step():
@@ -642,8 +651,10 @@ def probe_arm(args):
     row_ms = sum(ev[2 * r].elapsed_time(ev[2 * r + 1]) for r in range(rows)) / rows
     peaks = load_peaks()
     peak = (peaks or {}).get("hbm_gbs") or 6800.0
-    achieved = row_bytes / (row_ms / 1e3) / 1e9
-    traffic = load_traffic("gather_kernel:probe:square:L%d:D%d:P%d" % (L, D, P))
+    achieved = row_bytes / (row_ms / 1e3) / 1e9  # per-update algorithmic bytes (one factor at a time)
+    own = row_own / (row_ms / 1e3) / 1e9        # bytes the launched tables need
+    traffic = load_traffic("gather_kernel:probe:square:L%d:D%d:P%d:%s" % (L, D, P,
+                                                                          "site" if args.per_site_tables else "auto"))
     # e2e through the C ABI: the read-out copied to host memory every step
     host = None
     f0 = time.perf_counter()
@@ -665,13 +676,15 @@ def probe_arm(args):
                       "updates_per_step": upd_step},
            "e2e": {"value": upd_step * args.steps / (e2e_ms / 1e3), "unit": "updates/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 4 * P * (D + 1), "ms_per_step": e2e_ms / args.steps},
-           "gpu_launches": args.steps * (rows * len_row + (L - 1 if args.per_site_tables else L // 2) + 1),
+           "gpu_launches": args.steps * (rows * len_row + (L // 2 if paired else L - 1) + 1),
            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                         "frac": round(achieved / peak, 4),
                         "traffic": traffic["dram_bytes_per_launch"] if traffic else None,
                         "algorithmic_bytes_per_launch": row_bytes / len_row, "avg_launch_ms": row_ms / len_row,
                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800 GB/s",
-                        "kernel": "TMA gather (row advance = %d launches)" % len_row}}
+                        "kernel": "TMA gather (row advance = %d launches)" % len_row,
+                        "tables_own_bytes": {"bytes_per_launch": row_own / len_row, "achieved": round(own, 1),
+                                             "frac": round(own / peak, 4)}}}
     if clk:
         res["clocks"] = clk
     if pool is not None:
@@ -680,7 +693,7 @@ def probe_arm(args):
         pool.map(_probe_oracle_job, [(cL, rows, D, p) for p in primes[:cP]])
         wall = time.perf_counter() - t
         with cp.Strip("square", cL, primes[:1], max_degree=D, max_rows=rows + 1) as sc:
-            ru, _, ou, _ = sc.work()
+            ru, _, ou, _, _, _ = sc.work()
         cupd = (rows * ru + ou) * cP
         res["cpu_baseline"] = {"value": cupd / wall, "unit": "updates/s", "cores": cP, "kind": "oracle",
                                "sample": "plain-C mod-p oracle (hash-map TM), square width %d, %d rows, D=%d, %d "

@@ -116,13 +116,16 @@ int cp_read_coeffs_device(cp_strip *s, uint32_t *out_dev, size_t out_len);
  * intermediate space, *degree = D, *height = current height. */
 int cp_strip_info(const cp_strip *s, uint64_t n_states[2], int *degree, int *height);
 
-/* Work of the strip's per-site factors, for throughput and roofline figures:
+/* Work of the strip's factors, for throughput and roofline figures:
  * work[0] = updates of one row advance (output words of T_1 .. T_L: sum of
- * S_out (D+1) n_primes), work[1] = its algorithmic bytes (every factor reads
- * its input vector and writes its output vector once, 4 (S_in + S_out)(D+1)
- * n_primes, plus its CSR table, 4 (S_out + 1 + nnz)); work[2], work[3] = the
- * same for one read-out (T_1^last .. T_{L-1}^last).  No GPU work. */
-int cp_strip_work(const cp_strip *s, uint64_t work[4]);
+ * S_out (D+1) n_primes over the per-site factors), work[1] = the bytes its
+ * launched tables need (each reads its input vector and writes its output
+ * vector once, 4 (S_in + S_out)(D+1) n_primes, plus its CSR table,
+ * 4 (S_out + 1 + nnz); a two-site table skips the intermediate vector),
+ * work[2], work[3] = the same for one read-out (T_1^last .. T_{L-1}^last),
+ * work[4], work[5] = the bytes of the row and of the read-out done one factor
+ * at a time (intermediate vectors included).  No GPU work. */
+int cp_strip_work(const cp_strip *s, uint64_t work[6]);
 
 /* Restart the strip at height 1 with the state vector e_0 (keeps its tables
  * and buffers).  Asynchronous on the strip's stream. */
@@ -131,18 +134,22 @@ int cp_strip_reset(cp_strip *s);
 void cp_destroy(cp_strip *s);
 
 /*
- * cp_set_factor_pairing -- how the chromatic tables built from now on are laid
- * out (strips, sweeps and server jobs created afterwards; tables already built
- * stay cached under their own layout).  on = 1 (the default): one two-site
- * table per consecutive pair of per-site factors, T_2 T_1, T_4 T_3, ... of the
- * row and of the read-out chain (an odd one out stays single), so a row of L
- * sites takes ceil(L/2) gather launches and the intermediate vector of each
- * pair is never written: the same matrix product as the factorisation of
- * Sec. 3.2-3.3 with half the vector traffic.  on = 0: one table per factor, as
- * in the paper.  Results are identical either way.  Returns the previous
- * setting.  Not thread-safe against concurrent strip creation.
+ * cp_set_factor_pairing -- how the square-lattice chromatic tables built from
+ * now on are laid out (strips, sweeps and server jobs created afterwards;
+ * tables already built stay cached under their own layout).  A two-site table
+ * is the product of a consecutive pair of per-site factors, T_2 T_1, T_4 T_3,
+ * ... of the row and of the read-out chain (an odd one out stays single): a
+ * row of L sites takes ceil(L/2) gather launches and the intermediate vector
+ * of each pair is never written -- the same matrix product as the
+ * factorisation of Sec. 3.2 with half the vector traffic but as many edge
+ * copies, which pays only when a state's row, (D+1) n_primes words, is a few
+ * KB long.  mode 1 (the default): two-site tables for rows of at least 3 KB;
+ * mode 2: for every square-lattice strip; mode 0: one table per factor, as in
+ * the paper.  Triangular tables are always one per factor.  Results are
+ * identical in every mode.  Returns the previous mode.  Not thread-safe
+ * against concurrent strip creation.
  */
-int cp_set_factor_pairing(int on);
+int cp_set_factor_pairing(int mode);
 
 /*
  * cp_crt -- Chinese remaindering (Sec. 3.5): for each of n_coeffs
@@ -226,6 +233,14 @@ int cp_sweep_sync(cp_sweep *sw);
  * plus its CSR index; launches = batched gather launches + 1 series kernel. */
 int cp_sweep_info(const cp_sweep *sw, int *n_rects, int *n_terms, int *tile, int *prime_groups,
                   uint64_t *updates_per_run, uint64_t *bytes_per_run, int *launches_per_run);
+
+/* Work of one run in both accountings: work[0] = updates (output words of
+ * every per-site factor, as in cp_sweep_info), work[1] = bytes the launched
+ * tables need (input + output vector + CSR of each table, two-site tables
+ * included: as bytes_per_run), work[2] = bytes of the same work done one
+ * factor at a time (4 (S_in + S_out)(D+1) P for every per-site factor, the
+ * intermediate vectors of two-site tables included, plus the tables' CSR). */
+int cp_sweep_work(const cp_sweep *sw, uint64_t work[3]);
 
 /* The rectangles, rs_host[2j] = r, rs_host[2j+1] = s. */
 int cp_sweep_rects(const cp_sweep *sw, int *rs_host, int max_rects);

@@ -47,6 +47,7 @@ SIGNATURES = {
                                        vp, ctypes.POINTER(vp)]),
     "cp_sweep_run": (ctypes.c_int, [vp]),
     "cp_sweep_sync": (ctypes.c_int, [vp]),
+    "cp_sweep_work": (ctypes.c_int, [vp, u64p]),
     "cp_sweep_info": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), u64p, u64p,
                                      ctypes.POINTER(ctypes.c_int)]),
@@ -205,8 +206,9 @@ class Strip:
         check("cp_strip_reset", load().cp_strip_reset(self._h))
 
     def work(self):
-        """(row updates, row bytes, read-out updates, read-out bytes); see cp_strip_work."""
-        w = (ctypes.c_uint64 * 4)()
+        """(row updates, row bytes, read-out updates, read-out bytes, row bytes one factor at a
+        time, read-out bytes one factor at a time); see cp_strip_work."""
+        w = (ctypes.c_uint64 * 6)()
         check("cp_strip_work", load().cp_strip_work(self._h, w))
         return tuple(int(x) for x in w)
 
@@ -231,10 +233,11 @@ class Strip:
         self.close()
 
 
-def set_factor_pairing(on):
-    """Two-site tables (True, the default) or one table per site factor for tables
-    built from now on (cp_set_factor_pairing); returns the previous setting."""
-    return bool(load().cp_set_factor_pairing(1 if on else 0))
+def set_factor_pairing(mode):
+    """Layout of square-lattice tables built from now on (cp_set_factor_pairing): 0 one
+    table per site factor, 1 two-site tables for rows of at least 3 KB (default), 2
+    two-site tables always.  Returns the previous mode."""
+    return int(load().cp_set_factor_pairing(int(mode)))
 
 
 def debug_check_space(kind, m, e=0):
@@ -274,6 +277,9 @@ class Sweep:
         check("cp_sweep_info", load().cp_sweep_info(h, *[ctypes.byref(v) for v in vals]))
         (self.n_rects, self.n_terms, self.tile, self.prime_groups, self.updates_per_run, self.bytes_per_run,
          self.launches_per_run) = [v.value for v in vals]
+        w = (ctypes.c_uint64 * 3)()
+        check("cp_sweep_work", load().cp_sweep_work(h, w))
+        self.site_bytes_per_run = int(w[2])  # the same work one factor at a time
         rs = (ctypes.c_int * (2 * self.n_rects))()
         check("cp_sweep_rects", load().cp_sweep_rects(h, rs, self.n_rects))
         self.rects = [(rs[2 * j], rs[2 * j + 1]) for j in range(self.n_rects)]

@@ -126,11 +126,14 @@ int build_x_prefix(int m, int e, cudaStream_t st, uint32_t **out);
 
 // Build or fetch from the cache the tables of (lattice, L) on the current device
 // (chromatic polynomial: the projected factorisation of Sec. 3.2-3.3), paired
-// or not according to factor_pairing().
-int get_tables(int lattice, int L, cudaStream_t stream, std::shared_ptr<TableSet> *out);
-// Library-wide choice for tables built from now on: 1 = two-site tables (default), 0 = one per factor.
+// or not according to factor_pairing() and the row size.
+// row_bytes = bytes of one state's row, (D+1) * n_primes * 4, of the caller's vectors.
+int get_tables(int lattice, int L, size_t row_bytes, cudaStream_t stream, std::shared_ptr<TableSet> *out);
+// Library-wide choice for tables built from now on: 0 = one table per factor, 1 = two-site
+// square-lattice tables for rows of at least kPairRowBytes (default), 2 = every square table.
+constexpr size_t kPairRowBytes = 3072;
 int factor_pairing();
-int set_factor_pairing(int on);
+int set_factor_pairing(int mode);
 // Tables of the any-v Potts transfer matrix T_i = V_i H_{i,i+1} (square) or
 // V_i H_{i-1,i} H_{i,i+1} (triangular) on non-crossing partitions.
 int get_potts_tables(int lattice, int L, int v, cudaStream_t stream, std::shared_ptr<TableSet> *out);

@@ -30,7 +30,10 @@ constexpr int kTmaConsumers = 8;                      // consumer warps
 constexpr int kTmaThreads = 32 * (kTmaConsumers + 1);  // + producer warp
 constexpr int kTmaMaxSlots = 96;
 constexpr int kTmaMaxPasses = 8;                       // C <= 8 * 256 chunks
-constexpr uint32_t kIssueBatch = 2;                    // copies issued together by the producer warp
+// Copies the producer warp issues together: about kIssueBytes per batch, at
+// least 2 and at most kIssueBatchMax (narrow rows need more copies in flight).
+constexpr uint32_t kIssueBytes = 8192;
+constexpr uint32_t kIssueBatchMax = 16;
 constexpr long long kWaitCycles = 1ll << 31;           // ~1 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -158,14 +161,14 @@ __global__ void __launch_bounds__(kTmaThreads, PASSES == 1 ? 7 : (PASSES == 2 ? 
 
     if (warp == 0) {
         // ---------------- producer: one bulk copy per edge, in CSR order, the
-        // copies of kIssueBatch consecutive edges issued together, one lane per
-        // edge (a batch holds at most nsub edges of any sub-ring, so its slots
+        // copies of B consecutive edges issued together, one lane per edge
+        // (B <= nsub: a batch holds at most nsub edges of any sub-ring, so its slots
         // are distinct); a lane finds its edge's row by binary search of the
         // block's row pointers, hence the edge's sub-ring and position in it.
         // Issuing from several lanes keeps more copies in flight than one lane
         // walking the edges could.
         const uint32_t e_begin = s_rp[0], e_end = s_rp[nrows];
-        const uint32_t B = min(kIssueBatch, nsub);
+        const uint32_t B = min(nsub, min(kIssueBatchMax, max(2u, kIssueBytes / RB)));
         bool ok = true;
         uint32_t qn = (lane < B && e_begin + lane < e_end) ? __ldg(t.edges + e_begin + lane) : 0u;
         for (uint32_t base = e_begin; base < e_end && ok; base += B) {

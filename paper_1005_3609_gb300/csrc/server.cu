@@ -176,7 +176,7 @@ static int job_prime_limit(int D1) {
 static int admit(cp_server *sv, Job *j, bool *fits) {
     *fits = false;
     int rc;
-    if (!j->tabs && (rc = get_tables(j->lattice, j->L, sv->stream, &j->tabs))) return rc;
+    if (!j->tabs && (rc = get_tables(j->lattice, j->L, (size_t)j->D1 * j->P * 4, sv->stream, &j->tabs))) return rc;
     const TableSet &ts = *j->tabs;
     const size_t RB = (size_t)j->D1 * j->P * 4;
     j->bytes = request_bytes(ts, j->L, RB);

@@ -216,7 +216,8 @@ extern "C" int cp_create_strip(int lattice, int L, const uint32_t *primes, int n
     if (rc) return rc;
     if ((rc = prepare_gather_kernels())) return rc;
     std::shared_ptr<TableSet> tabs;
-    if ((rc = get_tables(lattice, L, (cudaStream_t)cuda_stream, &tabs))) return rc;
+    const long long D1 = max_degree >= 0 ? max_degree + 1 : (long long)L * max_rows;
+    if ((rc = get_tables(lattice, L, (size_t)D1 * n_primes * 4, (cudaStream_t)cuda_stream, &tabs))) return rc;
     return make_strip(std::move(tabs), lattice, L, primes, n_primes, max_degree, max_rows, cuda_stream, out);
 }
 
@@ -290,18 +291,20 @@ extern "C" int cp_strip_info(const cp_strip *s, uint64_t n_states[2], int *degre
     return CP_OK;
 }
 
-extern "C" int cp_strip_work(const cp_strip *s, uint64_t work[4]) {
+extern "C" int cp_strip_work(const cp_strip *s, uint64_t work[6]) {
     if (!s || !work) return fail(CP_EINVAL, "NULL argument");
     const uint64_t row = (uint64_t)s->D1 * s->P;  // words per state
-    work[0] = work[1] = work[2] = work[3] = 0;
-    for (const SiteTable &t : s->tabs->row) {
-        work[0] += t.n_site_out * row;
-        work[1] += 4 * (t.n_src + t.n_dst) * row + 4 * (t.n_dst + 1 + t.nnz);
-    }
-    for (const SiteTable &t : s->tabs->last) {
-        work[2] += t.n_site_out * row;
-        work[3] += 4 * (t.n_src + t.n_dst) * row + 4 * (t.n_dst + 1 + t.nnz);
-    }
+    for (int k = 0; k < 6; ++k) work[k] = 0;
+    // updates, own bytes, one-factor-at-a-time bytes -> work[u], work[b], work[f]
+    auto add = [&](const SiteTable &t, int u, int b, int f) {
+        const uint64_t mid = t.n_site_out - t.n_dst;  // intermediate states of a two-site table
+        const uint64_t csr = 4 * (t.n_dst + 1 + t.nnz);
+        work[u] += t.n_site_out * row;
+        work[b] += 4 * (t.n_src + t.n_dst) * row + csr;
+        work[f] += 4 * (t.n_src + 2 * mid + t.n_dst) * row + csr;
+    };
+    for (const SiteTable &t : s->tabs->row) add(t, 0, 1, 4);
+    for (const SiteTable &t : s->tabs->last) add(t, 2, 3, 5);
     return CP_OK;
 }
 

@@ -59,7 +59,7 @@ struct cp_sweep {
     GatherTask *tasks_dev = nullptr;
     std::vector<uint32_t> step_off, step_ntasks, step_blocks;
     std::vector<int> step_tile;
-    uint64_t updates = 0, bytes = 0;
+    uint64_t updates = 0, bytes = 0, site_bytes = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 
@@ -91,8 +91,10 @@ static int rect_index(const cp_sweep *sw, int r, int s) {
 // Accumulate the algorithmic work of one factor: output words, and bytes =
 // 4 (S_in + S_out) (D+1) Pg + CSR index bytes.
 static void count_work(cp_sweep *sw, const SiteTable &t, int Pg) {
+    const uint64_t mid = t.n_site_out - t.n_dst;  // intermediate states of a two-site table (else 0)
     sw->updates += t.n_site_out * (uint64_t)sw->D1 * Pg;
     sw->bytes += 4ull * (t.n_src + t.n_dst) * sw->D1 * Pg + 4ull * (t.n_dst + 1 + t.nnz);
+    sw->site_bytes += 4ull * (t.n_src + 2 * mid + t.n_dst) * sw->D1 * Pg + 4ull * (t.n_dst + 1 + t.nnz);
 }
 
 // Strips and buffers: one strip per width (and prime group), band rectangles.
@@ -113,7 +115,7 @@ static int build_strips(cp_sweep *sw) {
             for (auto &rs : sw->rects)
                 if (rs.x == r) st.heights.push_back(rs.y);
             if (st.heights.empty()) continue;
-            if ((rc = get_tables(sw->lattice, r, sw->stream, &st.tabs))) return rc;
+            if ((rc = get_tables(sw->lattice, r, row_words * 4, sw->stream, &st.tabs))) return rc;
             const TableSet &ts = *st.tabs;
             sw->strips.push_back(st);
             SweepStrip &sp = sw->strips.back();
@@ -137,7 +139,7 @@ static int build_program(cp_sweep *sw, int tile) {
     const size_t row_words = (size_t)sw->D1 * Pg;
     int rc;
     sw->tile = tile;
-    sw->updates = sw->bytes = 0;
+    sw->updates = sw->bytes = sw->site_bytes = 0;
     sw->step_off.clear();
     sw->step_ntasks.clear();
     sw->step_blocks.clear();
@@ -373,6 +375,14 @@ extern "C" int cp_sweep_sync(cp_sweep *sw) {
     int herr = 0;
     CP_CUDA_TRY(cudaMemcpy(&herr, sw->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
     if (herr) return fail(CP_ESTATE, "a rectangle's P~ lacks constant term 1");
+    return CP_OK;
+}
+
+extern "C" int cp_sweep_work(const cp_sweep *sw, uint64_t work[3]) {
+    if (!sw || !work) return fail(CP_EINVAL, "NULL argument");
+    work[0] = sw->updates;
+    work[1] = sw->bytes;
+    work[2] = sw->site_bytes;
     return CP_OK;
 }
 

@@ -723,34 +723,39 @@ static int build_potts_tableset(int lattice, int L, int v, cudaStream_t st, std:
 
 static std::mutex g_cache_mu;
 static std::map<std::tuple<int, int, int>, std::shared_ptr<TableSet>> g_cache[64];  // per device
-static int g_pairing = 1;
+static int g_pairing = 1;  // 0 never, 1 square rows of >= kPairRowBytes, 2 every square table
 
 int factor_pairing() {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     return g_pairing;
 }
 
-int set_factor_pairing(int on) {
+int set_factor_pairing(int mode) {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     const int old = g_pairing;
-    g_pairing = on ? 1 : 0;
+    g_pairing = mode < 0 ? 0 : (mode > 2 ? 2 : mode);
     return old;
 }
 static std::map<std::tuple<int, int, int>, std::shared_ptr<TableSet>> g_potts_cache[64];
 
-int get_tables(int lattice, int L, cudaStream_t st, std::shared_ptr<TableSet> *out) {
+int get_tables(int lattice, int L, size_t row_bytes, cudaStream_t st, std::shared_ptr<TableSet> *out) {
     int dev = 0;
     CP_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(CP_EINVAL, "device index");
     std::lock_guard<std::mutex> lk(g_cache_mu);
-    auto key = std::make_tuple(lattice, L, g_pairing);
+    // Two-site tables halve the vector traffic but not the number of edge copies,
+    // which set the pace on narrow rows: they pay on square-lattice rows of a few
+    // KB and more; on the triangular lattice a pair has up to 21 terms per source
+    // and the gathers ran slower than one factor at a time.
+    const int paired = lattice == CP_SQUARE && (g_pairing == 2 || (g_pairing == 1 && row_bytes >= kPairRowBytes));
+    auto key = std::make_tuple(lattice, L, paired);
     auto it = g_cache[dev].find(key);
     if (it != g_cache[dev].end()) {
         *out = it->second;
         return CP_OK;
     }
     std::shared_ptr<TableSet> ts;
-    int rc = build_tableset(lattice, L, g_pairing, st, &ts);
+    int rc = build_tableset(lattice, L, paired, st, &ts);
     if (rc) return rc;
     g_cache[dev][key] = ts;
     *out = ts;
