@@ -95,7 +95,8 @@ int cp_create_strip_potts(int lattice, int L, int v, const uint32_t *primes_host
 
 /*
  * cp_advance_rows -- apply T = T_L ... T_1 n_rows times (eq. (T_sq_decomp));
- * height += n_rows.  Asynchronous on the strip's stream (one kernel per site).
+ * height += n_rows.  Asynchronous on the strip's stream (one gather launch per
+ * table: per site, or per pair of sites with two-site tables).
  * Errors: CP_EINVAL (height would exceed max_rows), CP_ECUDA.
  */
 int cp_advance_rows(cp_strip *s, int n_rows);
@@ -261,7 +262,7 @@ int cp_sweep_read_series_device(cp_sweep *sw, uint32_t *out_dev, size_t out_len)
  * copy of n_primes words on the sweep's stream; the tables and the graph stay. */
 int cp_sweep_set_primes(cp_sweep *sw, const uint32_t *primes_host, int n_primes);
 
-/* Run the sweep's per-site launches once WITHOUT the graph, with a CUDA event
+/* Run the sweep's batched gather launches once WITHOUT the graph, with a CUDA event
  * pair around each batched gather launch on the sweep's stream: *gather_ms =
  * summed gather kernel time, *n_gather = launches, *total_ms = whole pass
  * (no series kernel).  Synchronises.  For roofline measurements. */
