@@ -154,3 +154,11 @@ def test_rejections():
     # the library is still usable afterwards
     assert run_potts("square", 3, 3, 16, primes).tolist() == gpu_util.residues_of(
         tm_generic.ztilde("square", 3, 3, 16), primes)
+
+
+def test_largest_coupling():
+    # v = 16 at widths whose spaces leave 14 coefficient bits: (1+v)^2 v = 4624 fits
+    primes = gpu_util.seed_primes(4, seed=12)
+    for lattice, L, N in (("triangular", 8, 3), ("square", 9, 3)):
+        want = tm_generic.ztilde(lattice, L, N, 16)
+        assert run_potts(lattice, L, N, 16, primes).tolist() == gpu_util.residues_of(want, primes), lattice
