@@ -63,3 +63,26 @@ def test_argument_errors_without_gpu(lib):
     assert lib.cp_create_strip(0, 4, bad, 1, -1, 2, None, ctypes.byref(h)) == -1
     assert b"prime" in lib.cp_last_error()
     assert lib.cp_advance_rows(None, 1) == -1
+
+
+def test_newer_entry_points_validate_without_gpu(lib):
+    # the Potts strip, the pairing switch and the work queries check their arguments first
+    import ctypes
+    from paper_1005_3609_gb300 import _lib
+    h = ctypes.c_void_p()
+    one = (ctypes.c_uint32 * 1)(1073741827)
+    src = open(os.path.join(ROOT, "include", "cp_tm.h")).read()
+    vmax = int(re.search(r"#define CP_POTTS_MAX_V (\d+)", src).group(1))
+    lmax = int(re.search(r"#define CP_POTTS_MAX_L (\d+)", src).group(1))
+    assert lib.cp_create_strip_potts(0, 4, vmax + 1, one, 1, -1, 2, None, ctypes.byref(h)) == -1
+    assert b"v must be" in lib.cp_last_error()
+    assert lib.cp_create_strip_potts(1, lmax + 1, 2, one, 1, -1, 2, None, ctypes.byref(h)) == -1
+    assert lib.cp_create_strip_potts(2, 4, 2, one, 1, -1, 2, None, ctypes.byref(h)) == -1  # lattice
+    assert lib.cp_create_strip_potts(0, 4, 2, one, 1, -1, 0, None, ctypes.byref(h)) == -1  # max_rows
+    assert lib.cp_strip_work(None, (ctypes.c_uint64 * 6)()) == -1
+    assert lib.cp_sweep_work(None, (ctypes.c_uint64 * 3)()) == -1
+    # the pairing switch returns the previous mode and clamps to 0..2
+    old = lib.cp_set_factor_pairing(0)
+    assert old in (0, 1, 2)
+    assert lib.cp_set_factor_pairing(7) == 0
+    assert lib.cp_set_factor_pairing(old) == 2
