@@ -189,10 +189,11 @@ def table_layout(cp, args):
 
 
 def tile_name(tile):
-    rows, ring, passes = tile & 0xFFF, (tile >> 12) & 0xFF, (tile >> 20) & 7
+    rows, ring, edges = tile & 0xFFF, (tile >> 12) & 0xFF, (tile >> 20) & 15
     if rows <= 8:
         return "register gather kernel, %d rows/warp" % rows
-    return "TMA gather kernel, %d rows/block, %d KB ring, %d chunk(s)/thread" % (rows, ring or 28, passes or 1)
+    return "TMA gather kernel, %d rows/block, %d KB ring, %s edge(s) per stage" % (rows, ring or 32,
+                                                                                 edges or "auto")
 
 
 def plain_run(cp, torch, lattice, k, primes, stream):

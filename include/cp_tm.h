@@ -41,7 +41,8 @@ enum {
     CP_ENOMEM = -2,   /* device or host allocation failed / over budget */
     CP_ECUDA = -3,    /* a CUDA call failed                             */
     CP_ETIMEOUT = -4, /* a bounded device wait ran out                  */
-    CP_ESTATE = -5    /* internal consistency check failed              */
+    CP_ESTATE = -5,   /* internal consistency check failed              */
+    CP_EPRIMES = -6   /* too few primes for an exact integer result     */
 };
 
 #define CP_MAX_L 20       /* widest strip compiled in (the paper's m_max = 20, Sec. 4.2) */
@@ -157,11 +158,57 @@ int cp_set_factor_pairing(int mode);
  * coefficients, residues_host[k*n_coeffs + j] modulo primes_host[k] ->
  * the integer in (-prod/2, prod/2], written as limbs_per_coeff little-endian
  * 32-bit limbs in two's complement: limbs_host[j*limbs_per_coeff + l].
- * Runs on the GPU (Garner's mixed radix, one thread per coefficient).
- * Errors: CP_EINVAL if limbs_per_coeff*32 < bits(prod)+1.
+ * Runs on the GPU (Garner's mixed radix, one thread per coefficient).  It
+ * returns whatever the given primes determine: an integer of magnitude
+ * prod/2 or more comes back reduced; cp_crt_checked says when that may be so.
+ * Errors: CP_EINVAL if limbs_per_coeff * 32 is below the bit length of
+ * prod(primes) plus 1 (computed exactly), or bad primes.
  */
 int cp_crt(const uint32_t *residues_host, const uint32_t *primes_host, int n_primes,
            int n_coeffs, uint32_t *limbs_host, int limbs_per_coeff);
+
+/*
+ * cp_crt_checked -- cp_crt plus the two sufficiency checks of the
+ * reconstruction (Sec. 3.5: primes are added until the result stops changing).
+ * Per coefficient j, flags_host[j] (optional, may be NULL) gets
+ *   bit 0: bound_bits_host is given and bound_bits_host[j] + 2 exceeds the bit
+ *          length of prod(primes), i.e. a coefficient with |c_j| < 2^bound_bits
+ *          is not guaranteed to lie in the recovered range (-prod/2, prod/2);
+ *   bit 1: the value recombined from the first n_primes - 1 primes differs
+ *          from the one from all n_primes (always set for n_primes = 1).
+ * bound_bits_host may be NULL (stabilisation check only); for chromatic
+ * polynomials cp_whitney_bits gives a valid bound.  The limbs are written in
+ * any case; the return is CP_EPRIMES ("not enough primes", with the counts in
+ * cp_last_error()) if any flag is set, else CP_OK.  Other errors as cp_crt.
+ */
+int cp_crt_checked(const uint32_t *residues_host, const uint32_t *primes_host, int n_primes, int n_coeffs,
+                   const uint32_t *bound_bits_host, uint32_t *limbs_host, int limbs_per_coeff,
+                   uint32_t *flags_host);
+
+/*
+ * cp_whitney_bits -- bits_host[j] = bit length of C(|E|, j), j < n_coeffs, for
+ * the L x N rectangle of the lattice (|E| = L(N-1) + N(L-1), plus (L-1)(N-1)
+ * diagonals on the triangular lattice).  By Whitney's broken-circuit theorem
+ * the coefficient of q^{|V|-j} in P_G(q), which is c_j of P~ (eq.
+ * (Z_modified)), satisfies |c_j| <= C(|E|, j), so these are bounds for
+ * cp_crt_checked.  Exact integer arithmetic on the host; no GPU work.
+ */
+int cp_whitney_bits(int lattice, int L, int N, int n_coeffs, uint32_t *bits_host);
+
+/*
+ * cp_read_integers -- the exact integer coefficients c_0..c_D of the strip's
+ * P~ (L x height): the read-out of cp_read_coeffs, then the CRT over the
+ * strip's primes on the GPU with both checks of cp_crt_checked (chromatic
+ * strips: Whitney's bound for L x height and stabilisation; Potts strips:
+ * stabilisation only).  Writes limbs_host[j*limbs_per_coeff + l] (limbs_len >=
+ * (D+1)*limbs_per_coeff), flags_host[0..D] if not NULL, *height_out if not
+ * NULL; synchronises the strip's stream.  Returns CP_EPRIMES when the strip's
+ * primes are too few for an exact result (the limbs are still written).
+ * Errors: CP_EINVAL (sizes, limbs_per_coeff too small for the prime product),
+ * CP_ENOMEM, CP_ECUDA, CP_ETIMEOUT.
+ */
+int cp_read_integers(cp_strip *s, uint32_t *limbs_host, size_t limbs_len, int limbs_per_coeff,
+                     uint32_t *flags_host, int *height_out);
 
 /* Device-memory variant of cp_crt (asynchronous on cuda_stream). */
 int cp_crt_device(const uint32_t *residues_dev, const uint32_t *primes_host, int n_primes,
@@ -176,14 +223,19 @@ int cp_crt_device(const uint32_t *residues_dev, const uint32_t *primes_host, int
  * arguments, result and errors as cp_crt.  The residues and limbs are staged in
  * one fixed device array of CP_CRT_STATIC_BYTES bytes (residues rounded up to
  * 256 bytes, then limbs); a call needing more returns CP_EINVAL with the sizes
- * in cp_last_error().  The array is created when the library is loaded, once
- * per device, and held until the process exits.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Synchronous (legacy
- * default stream).  All calls share the array and it keeps the last call's
- * contents (every limb is rewritten, nothing needs clearing), so calls that
- * overlap on the GPU -- from several host threads at once -- race; serialise
- * them.
+ * in cp_last_error().  The array lives in the library's CRT device module.
+ * CUDA loads a module onto a device lazily, when the module is first used
+ * there, and that is when the array's 8 MiB are taken on that device (held
+ * until the process exits): the first cp_crt_static call on the device, or any
+ * earlier cp_select_primes, cp_crt*, cp_create_strip*, cp_sweep_create or
+ * cp_server_create call there.  A caller whose allocator is about to take the
+ * rest of the device memory makes one of these calls on each device first.
+ * Each call looks up the array's device address (cudaGetSymbolAddress) with
+ * the calling thread's current device, so the first call on a device should
+ * come before any stream capture.  Synchronous (legacy default stream).  All
+ * calls share the array and it keeps the last call's contents (every limb is
+ * rewritten, nothing needs clearing), so calls that overlap on the GPU -- from
+ * several host threads at once -- race; serialise them.
  */
 #define CP_CRT_STATIC_BYTES (8u << 20)
 int cp_crt_static(const uint32_t *residues_host, const uint32_t *primes_host, int n_primes,
@@ -254,6 +306,15 @@ int cp_sweep_read_ptilde(cp_sweep *sw, uint32_t *out_host, size_t out_len);
  * Table 1; triangular: (1-x)^2 exp(f_b)/q, Baxter's product eq. (efb)),
  * x = 1 exp(f_s), x = 2 exp(f_c); modulo primes[k].  Synchronises. */
 int cp_sweep_read_series(cp_sweep *sw, uint32_t *out_host, size_t out_len);
+
+/* The three series as exact integers, CRT'd over the sweep's primes on the GPU:
+ * limbs_host[(x*n_terms + i)*limbs_per_coeff + l] (limbs_len >= 3*n_terms*
+ * limbs_per_coeff), series order as cp_sweep_read_series, and flags_host[x*n_terms
+ * + i] (optional) as cp_crt_checked's bit 1 (the value from the first n_primes - 1
+ * primes differs: not yet stable, Sec. 3.5).  Copies only the limbs (and flags)
+ * to the host; synchronises.  CP_EPRIMES if any term is not stable. */
+int cp_sweep_series_integers(cp_sweep *sw, uint32_t *limbs_host, size_t limbs_len, int limbs_per_coeff,
+                             uint32_t *flags_host);
 
 /* As cp_sweep_read_series into device memory, asynchronous on the sweep's stream. */
 int cp_sweep_read_series_device(cp_sweep *sw, uint32_t *out_dev, size_t out_len);
@@ -343,6 +404,15 @@ int cp_debug_check_space(int kind, int m, int e, uint64_t *n_bad, uint64_t *size
  * word is read and cleared), leaving the context usable.  For testing the
  * timeout path without faulting or hanging the GPU. */
 int cp_debug_wait_timeout(long long cycles);
+
+/* The modular reduction of the gather kernels (Sec. 3.5: arithmetic modulo
+ * primes below 2^31), run on the GPU on given values: out_host[k] =
+ * v_host[k] mod p_host[k] in [0, p), computed exactly as the kernels reduce an
+ * accumulator (integer Barrett step from the bias p 2^21, see the kernels'
+ * source).  Requires 2 <= p_host[k] < 2^31 and |v_host[k]| < p_host[k] * 2^20
+ * (the bound the table build enforces on every destination); CP_EINVAL
+ * otherwise.  Synchronous. */
+int cp_debug_reduce(const int64_t *v_host, const uint32_t *p_host, int n, uint32_t *out_host);
 
 /* Partitions of the space in rank order, as canonical labels:
  * out_host[r*m + i] = block label of site i (first-occurrence order).

@@ -14,7 +14,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libcp_gb300.so")
 
 CP_SQUARE, CP_TRIANGULAR = 0, 1
 LATTICES = {"square": CP_SQUARE, "triangular": CP_TRIANGULAR}
-STATUS = {0: "CP_OK", -1: "CP_EINVAL", -2: "CP_ENOMEM", -3: "CP_ECUDA", -4: "CP_ETIMEOUT", -5: "CP_ESTATE"}
+STATUS = {0: "CP_OK", -1: "CP_EINVAL", -2: "CP_ENOMEM", -3: "CP_ECUDA", -4: "CP_ETIMEOUT", -5: "CP_ESTATE",
+          -6: "CP_EPRIMES"}
+CP_EPRIMES = -6
 CP_MAX_L = 20
 CP_MAX_PRIMES = 32
 
@@ -69,11 +71,16 @@ SIGNATURES = {
     "cp_server_poll": (ctypes.c_int, [vp, u64p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "cp_server_cancel": (ctypes.c_int, [vp, ctypes.c_uint64]),
     "cp_debug_wait_timeout": (ctypes.c_int, [ctypes.c_longlong]),
+    "cp_debug_reduce": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64), u32p, ctypes.c_int, u32p]),
     "cp_server_stats": (ctypes.c_int, [vp, u64p, u64p, u64p, ctypes.POINTER(ctypes.c_size_t)]),
     "cp_server_destroy": (None, [vp]),
     "cp_crt": (ctypes.c_int, [u32p, u32p, ctypes.c_int, ctypes.c_int, u32p, ctypes.c_int]),
     "cp_crt_device": (ctypes.c_int, [vp, u32p, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp]),
     "cp_crt_static": (ctypes.c_int, [u32p, u32p, ctypes.c_int, ctypes.c_int, u32p, ctypes.c_int]),
+    "cp_crt_checked": (ctypes.c_int, [u32p, u32p, ctypes.c_int, ctypes.c_int, u32p, u32p, ctypes.c_int, u32p]),
+    "cp_whitney_bits": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, u32p]),
+    "cp_read_integers": (ctypes.c_int, [vp, u32p, ctypes.c_size_t, ctypes.c_int, u32p, ctypes.POINTER(ctypes.c_int)]),
+    "cp_sweep_series_integers": (ctypes.c_int, [vp, u32p, ctypes.c_size_t, ctypes.c_int, u32p]),
     "cp_select_primes": (ctypes.c_int, [u64p, ctypes.c_int, ctypes.c_int, u32p]),
     "cp_clear_table_cache": (None, []),
     "cp_last_error": (ctypes.c_char_p, []),
@@ -147,6 +154,36 @@ def crt(residues, primes, limbs_per_coeff=None):
     return limbs_to_ints(out)
 
 
+def limbs_for(n_primes):
+    """Limbs per coefficient that hold any value the n_primes primes (< 2^31) determine."""
+    return (31 * n_primes + 2 + 31) // 32 + 1
+
+
+def crt_checked(residues, primes, bound_bits=None, limbs_per_coeff=None):
+    """cp_crt_checked: (integers, flags, status) -- status 0 or CP_EPRIMES (too few primes)."""
+    res, rp = _u32(residues)
+    pr, pp = _u32(primes)
+    P, n = res.shape
+    limbs_per_coeff = limbs_per_coeff or limbs_for(P)
+    out = np.zeros((n, limbs_per_coeff), dtype=np.uint32)
+    flags = np.zeros(n, dtype=np.uint32)
+    bp = None
+    if bound_bits is not None:
+        bb, bp = _u32(bound_bits)
+    rc = load().cp_crt_checked(rp, pp, P, n, bp, out.ctypes.data_as(u32p), limbs_per_coeff,
+                               flags.ctypes.data_as(u32p))
+    if rc not in (0, CP_EPRIMES):
+        check("cp_crt_checked", rc)
+    return limbs_to_ints(out), [int(f) for f in flags], rc
+
+
+def whitney_bits(lattice, L, N, n_coeffs):
+    """Bit lengths of C(|E|, j), j < n_coeffs, for the L x N rectangle (cp_whitney_bits)."""
+    out = np.zeros(n_coeffs, dtype=np.uint32)
+    check("cp_whitney_bits", load().cp_whitney_bits(lattice_id(lattice), L, N, n_coeffs, out.ctypes.data_as(u32p)))
+    return [int(x) for x in out]
+
+
 def crt_static(residues, primes, limbs_per_coeff=None):
     """As crt(), through cp_crt_static (no device allocation; fixed-size staging array)."""
     res, rp = _u32(residues)
@@ -202,6 +239,21 @@ class Strip:
         check("cp_read_coeffs", load().cp_read_coeffs(self._h, out.ctypes.data_as(u32p), out.size, ctypes.byref(h)))
         return out
 
+    def read_integers(self, limbs_per_coeff=None, strict=True):
+        """Exact integer coefficients c_0..c_D of P~ (cp_read_integers): read-out, CRT and
+        the sufficiency checks on the GPU.  strict: raise CPError(CP_EPRIMES) when the
+        primes are too few; else return (integers, flags, status)."""
+        lpc = limbs_per_coeff or limbs_for(len(self.primes))
+        out = np.zeros((self.degree + 1, lpc), dtype=np.uint32)
+        flags = np.zeros(self.degree + 1, dtype=np.uint32)
+        h = ctypes.c_int()
+        rc = load().cp_read_integers(self._h, out.ctypes.data_as(u32p), out.size, lpc, flags.ctypes.data_as(u32p),
+                                     ctypes.byref(h))
+        if strict or rc not in (0, CP_EPRIMES):
+            check("cp_read_integers", rc)
+            return limbs_to_ints(out)
+        return limbs_to_ints(out), [int(f) for f in flags], rc
+
     def reset(self):
         check("cp_strip_reset", load().cp_strip_reset(self._h))
 
@@ -244,6 +296,16 @@ def debug_check_space(kind, m, e=0):
     bad, size = ctypes.c_uint64(), ctypes.c_uint64()
     check("cp_debug_check_space", load().cp_debug_check_space(kind, m, e, ctypes.byref(bad), ctypes.byref(size)))
     return int(bad.value), int(size.value)
+
+
+def debug_reduce(values, primes):
+    """The gather kernels' modular reduction on the GPU: [v mod p for v, p in zip(values, primes)]."""
+    v = np.ascontiguousarray(np.asarray(values, dtype=np.int64))
+    p, pp = _u32(primes)
+    out = np.zeros(len(v), dtype=np.uint32)
+    check("cp_debug_reduce", load().cp_debug_reduce(v.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), pp, len(v),
+                                                    out.ctypes.data_as(u32p)))
+    return [int(x) for x in out]
 
 
 def debug_enumerate_space(kind, m, e=0, max_states=1 << 22):
@@ -316,10 +378,16 @@ class Sweep:
     def read_series_device(self, ptr, n_words):
         check("cp_sweep_read_series_device", load().cp_sweep_read_series_device(self._h, vp(ptr), n_words))
 
-    def series_integers(self):
-        """The three series as exact integers (cp_crt over all primes)."""
-        res = self.read_series()
-        return [crt(res[x], self.primes) for x in range(3)]
+    def series_integers(self, limbs_per_coeff=None, out=None):
+        """The three series as exact integers, CRT'd and checked for stability on the GPU
+        (cp_sweep_series_integers); raises CPError(CP_EPRIMES) if a term is not stable.
+        out: optional uint32 array [3][n_terms][limbs] (e.g. pinned) to receive the limbs."""
+        lpc = limbs_per_coeff or limbs_for(len(self.primes))
+        if out is None:
+            out = np.zeros((3, self.n_terms, lpc), dtype=np.uint32)
+        check("cp_sweep_series_integers", load().cp_sweep_series_integers(
+            self._h, out.ctypes.data_as(u32p), out.size, lpc, None))
+        return [limbs_to_ints(out[x]) for x in range(3)]
 
     def close(self):
         if self._h:

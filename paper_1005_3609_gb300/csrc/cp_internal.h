@@ -169,12 +169,11 @@ void append_gather_tasks(std::vector<GatherTask> *tasks, const SiteTable &tab, c
 // Gather tile (low 12 bits): 1, 2, 4, 8 = register kernel with that many rows
 // per warp (8 warps per block); 16, 32, 64, 128 = TMA kernel with that many rows
 // per block.  For TMA tiles, bits 12..19 = ring size in KB (0: default) and
-// bits 20..23 = chunks per consumer thread, 1, 2, 4 or 8 (0: 1).  A batch whose
-// rows are not all 16-byte chunked (or too wide for the ring) uses the
-// register kernel.
-constexpr int kTmaRingKbDefault = 28;
-inline int make_tile(int rows, int ring_kb, int passes = 1) { return rows | (ring_kb << 12) | (passes << 20); }
-inline int tile_passes(int tile) { int p = (tile >> 20) & 15; return p ? p : 1; }
+// bits 20..23 = edges per stage, 1, 2 or 4 (0: picked from the row size).  A
+// batch whose rows are not all 16-byte chunked uses the register kernel.
+constexpr int kTmaRingKbDefault = 32;
+inline int make_tile(int rows, int ring_kb, int edges = 0) { return rows | (ring_kb << 12) | (edges << 20); }
+inline int tile_edges(int tile) { return (tile >> 20) & 15; }
 inline int tile_ring_kb(int tile) { int r = (tile >> 12) & 0xFF; return r ? r : kTmaRingKbDefault; }
 bool tile_is_tma(int items);
 bool tma_usable(const GatherTask &t);
@@ -194,6 +193,21 @@ int check_device_error(cudaStream_t st);
 
 // Extract the e0 row laid out [D1][P] into [P][D1].
 int launch_transpose_row(const uint32_t *row, uint32_t *out, int D1, int P, cudaStream_t st);
+
+// ------------------------------------------------------------------ CRT (crt.cu)
+// Device CRT of residues [P][n_coeffs] into limbs [n_coeffs][limbs]; with
+// flags_dev, per-coefficient flags (bit 0: bound_dev[j] + 2 > bit length of the
+// prime product; bit 1: the first P-1 primes give another value).
+int launch_crt(const uint32_t *res_dev, const uint32_t *primes_host, int P, int n_coeffs, uint32_t *limbs_dev,
+               int limbs, const uint32_t *bound_dev, uint32_t *flags_dev, cudaStream_t st);
+int primes_product_bits(const uint32_t *primes, int P);
+// Bit lengths of C(n_edges, j), j < n_coeffs (Whitney's bound |c_j| <= C(|E|, j)).
+void binomial_bits(uint64_t n_edges, int n_coeffs, uint32_t *bits_out);
+uint64_t rectangle_edges(int lattice, int L, int N);
+// CP_OK if no flag is set, else CP_EPRIMES with a message counting them.
+int crt_verdict(const uint32_t *flags, int n_coeffs);
+// Load the CRT module (and the static array of cp_crt_static) on the current device.
+int crt_static_touch();
 
 // Device allocation helpers (library-owned memory).
 int dev_alloc(void **p, size_t bytes);

@@ -8,8 +8,9 @@
 // [state][degree][prime], so a shift by one degree is a shift by n_primes
 // words and, for n_primes % 4 == 0, every access is an aligned 16-byte load
 // that reads four primes of one degree.  The coefficients are exact integers:
-// each term coef * x (|coef| <= 4, x < p < 2^31) is added to a signed 64-bit
-// accumulator and the sum is reduced modulo p once per word (Sec. 3.5).
+// each term coef * x (x < p < 2^31) is added to a signed 64-bit accumulator and
+// the sum is reduced modulo p once per word (Sec. 3.5), in integer arithmetic
+// only (modred.cuh).
 //
 // One launch processes a batch of independent tasks (factors of different
 // strips); each block belongs to one task and covers 8 * RPW consecutive
@@ -20,18 +21,12 @@
 #include <string>
 
 #include "cp_internal.h"
+#include "modred.cuh"
 
 namespace cp {
 
-// v mod p for |v| < p * sum|coef| <= p * 2^20 (the table build enforces the
-// bound).  The quotient estimate fl(fl(v) * fl(1/p) - 1/2), fused, is within
-// 1/4 of v/p - 1/2 (relative error of the product < 3 * 2^-24 on |v/p| < 2^20,
-// plus half an ulp below 2^20), so its floor q' gives v - q' p in (p/4, 7p/4),
-// below 2^32 for p < 2^31, and one conditional subtraction finishes.
-__device__ __forceinline__ uint32_t reduce_s64(long long v, uint32_t p, float invp) {
-    const int q = __float2int_rd(__fmaf_rn(__ll2float_rn(v), invp, -0.5f));
-    const uint32_t r = (uint32_t)v - (uint32_t)q * p;
-    return min(r, r - p);
+__device__ __forceinline__ uint32_t reduce(long long acc, const ModRed &mr) {
+    return modred_reduce(acc, mr.p, mr.m, mr.s);
 }
 
 __device__ __forceinline__ int edge_coef(uint32_t e, uint32_t sb) { return (int)e >> (sb + 2); }
@@ -79,8 +74,7 @@ __device__ __forceinline__ void gather_edges(const GatherTask &t, uint32_t my, i
 // shuffles; the lanes sweep the row's chunks 32 at a time.  The next row's
 // CSR is fetched while the current row is computed.
 template <int RPW, bool V4>
-__device__ __forceinline__ void gather_rows(const GatherTask &t, uint32_t row0, const uint32_t *s_p,
-                                            const float *s_inv) {
+__device__ __forceinline__ void gather_rows(const GatherTask &t, uint32_t row0, const ModRed *s_mr) {
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t row = row0 + warp;
     uint32_t rp = (row < t.rows && lane < 2) ? __ldg(t.row_ptr + row + lane) : 0;
@@ -96,23 +90,22 @@ __device__ __forceinline__ void gather_rows(const GatherTask &t, uint32_t row0, 
             const uint32_t c = j + lane;
             const bool active = c < t.c0 + t.cw;
             const uint32_t deg = fast_div(c, t.magic_cpd);
-            long long acc[4] = {0, 0, 0, 0};
+            const uint32_t pc = (c - deg * t.cpd) * (V4 ? 4 : 1);  // prime of the first word
+            long long acc[4] = {modred_bias(s_mr[pc].p), V4 ? modred_bias(s_mr[pc + 1].p) : 0,
+                                V4 ? modred_bias(s_mr[pc + 2].p) : 0, V4 ? modred_bias(s_mr[pc + 3].p) : 0};
             gather_edges<V4>(t, my, (int)min(ne, 32u), c, deg, active, acc);
             for (uint32_t eb = 32; eb < ne; eb += 32) {  // rows with more than 32 edges
                 const uint32_t mb = (eb + lane < ne) ? __ldg(t.edges + e0 + eb + lane) : 0;
                 gather_edges<V4>(t, mb, (int)min(ne - eb, 32u), c, deg, active, acc);
             }
             if (active) {
-                const uint32_t pc = (c - deg * t.cpd) * (V4 ? 4 : 1);
                 const size_t o = (size_t)row * t.C + c;
                 if (V4) {
-                    const uint4 r = make_uint4(reduce_s64(acc[0], s_p[pc], s_inv[pc]),
-                                               reduce_s64(acc[1], s_p[pc + 1], s_inv[pc + 1]),
-                                               reduce_s64(acc[2], s_p[pc + 2], s_inv[pc + 2]),
-                                               reduce_s64(acc[3], s_p[pc + 3], s_inv[pc + 3]));
+                    const uint4 r = make_uint4(reduce(acc[0], s_mr[pc]), reduce(acc[1], s_mr[pc + 1]),
+                                               reduce(acc[2], s_mr[pc + 2]), reduce(acc[3], s_mr[pc + 3]));
                     __stcs(reinterpret_cast<uint4 *>(t.out) + o, r);
                 } else {
-                    __stcs(t.out + o, reduce_s64(acc[0], s_p[pc], s_inv[pc]));
+                    __stcs(t.out + o, reduce(acc[0], s_mr[pc]));
                 }
             }
         }
@@ -125,8 +118,7 @@ __device__ __forceinline__ void gather_rows(const GatherTask &t, uint32_t row0, 
 
 template <int RPW>
 __global__ void __launch_bounds__(kGatherThreads) gather_kernel(const GatherTask *__restrict__ tasks, int n_tasks) {
-    __shared__ uint32_t s_p[CP_MAX_PRIMES];
-    __shared__ float s_inv[CP_MAX_PRIMES];
+    __shared__ ModRed s_mr[CP_MAX_PRIMES];
     // task of this block: the last one whose block_begin <= blockIdx.x (block-uniform)
     int lo = 0, hi = n_tasks - 1;
     const uint32_t b = blockIdx.x;
@@ -136,15 +128,13 @@ __global__ void __launch_bounds__(kGatherThreads) gather_kernel(const GatherTask
     }
     const GatherTask t = tasks[lo];
     if (threadIdx.x < t.n_primes) {
-        const uint32_t p = __ldg(t.primes + threadIdx.x);
-        s_p[threadIdx.x] = p;
-        s_inv[threadIdx.x] = 1.0f / (float)p;
+        s_mr[threadIdx.x] = modred_make(__ldg(t.primes + threadIdx.x));
     }
     __syncthreads();
     // rows of the block: row0 + warp + 8 k, k < RPW
     const uint32_t row0 = (b - t.block_begin) * (uint32_t)(kWarps * RPW);
-    if (t.vec4) gather_rows<RPW, true>(t, row0, s_p, s_inv);
-    else gather_rows<RPW, false>(t, row0, s_p, s_inv);
+    if (t.vec4) gather_rows<RPW, true>(t, row0, s_mr);
+    else gather_rows<RPW, false>(t, row0, s_mr);
 }
 
 bool tile_is_tma(int items) { return (items & 0xFFF) >= 16; }
@@ -154,23 +144,26 @@ uint32_t task_blocks(const GatherTask &t, int items) {
     return (t.rows + per - 1) / per;
 }
 
-// For TMA tiles the requested chunks per thread (bits 20..21: 0 = 1) are raised
-// to what the widest row of the batch needs (C <= 256 * passes), and the ring
-// size defaults; a batch the TMA kernel cannot take uses the register kernel.
+// For TMA tiles: edges per stage (bits 20..23) default to about 8 KB of rows per
+// stage, and the ring is raised to hold at least two stages of the widest row
+// group; a batch the TMA kernel cannot take uses the register kernel.
 int effective_tile(const std::vector<GatherTask> &tasks, int items) {
     if (!tile_is_tma(items)) return items & 0xFFF;
-    int passes = tile_passes(items);
     uint32_t max_rb = 0;
     for (auto &t : tasks) {
         if (!tma_usable(t)) return kGatherItems;
-        while ((uint32_t)passes * 256u < t.cw) passes *= 2;
         max_rb = std::max(max_rb, t.cw * 16u);
+    }
+    int edges = tile_edges(items);
+    if (edges != 1 && edges != 2 && edges != 4) {
+        const uint32_t per = max_rb ? 8192u / max_rb : 4u;
+        edges = per >= 4 ? 4 : (per >= 2 ? 2 : 1);
     }
     int ring = (items >> 12) & 0xFF;
     if (!ring) ring = kTmaRingKbDefault;
-    // >= 16 KB and >= 4 rows: at least 4 slots per consumer group (G groups need rows <= 512 / G chunks)
-    ring = std::min(192, std::max(ring, std::max(16, (int)((4u * max_rb + 1023u) / 1024u))));
-    return make_tile(items & 0xFFF, ring, passes);
+    // a row group spans at most 4 KB of slot (G rows of cw chunks, G cw <= 256): two stages need 8 KB per edge
+    ring = std::min(192, std::max(ring, std::max(16, 8 * edges)));
+    return make_tile(items & 0xFFF, ring, edges);
 }
 
 uint32_t assign_blocks(std::vector<GatherTask> &tasks, int items) {
@@ -211,14 +204,14 @@ void append_gather_tasks(std::vector<GatherTask> *tasks, const SiteTable &tab, c
 }
 
 int launch_gather_tma(const GatherTask *tasks_dev, int n_tasks, uint32_t total_blocks, int rpb, int *err,
-                      cudaStream_t st, int passes, int ring_kb);
+                      cudaStream_t st, int edges, int ring_kb);
 int prepare_gather_tma();
 
 int launch_gather(const GatherTask *tasks_dev, int n_tasks, uint32_t total_blocks, int items, cudaStream_t st) {
     if (n_tasks <= 0 || total_blocks == 0) return CP_OK;
     if (tile_is_tma(items))
         return launch_gather_tma(tasks_dev, n_tasks, total_blocks, items & 0xFFE, device_error_flag(), st,
-                                 tile_passes(items), tile_ring_kb(items));
+                                 tile_edges(items), tile_ring_kb(items));
     switch (items & 0xFFF) {
         case 1: gather_kernel<1><<<total_blocks, kGatherThreads, 0, st>>>(tasks_dev, n_tasks); break;
         case 2: gather_kernel<2><<<total_blocks, kGatherThreads, 0, st>>>(tasks_dev, n_tasks); break;
@@ -278,4 +271,45 @@ int launch_transpose_row(const uint32_t *row, uint32_t *out, int D1, int P, cuda
     return CP_OK;
 }
 
+// Diagnostic: the gathers' reduction applied to given accumulator values.
+__global__ void debug_reduce_kernel(const long long *v, const uint32_t *p, int n, uint32_t *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const ModRed mr = modred_make(p[k]);
+    out[k] = reduce(modred_bias(mr.p) + v[k], mr);
+}
+
 }  // namespace cp
+
+extern "C" int cp_debug_reduce(const int64_t *v_host, const uint32_t *p_host, int n, uint32_t *out_host) {
+    using namespace cp;
+    if (n < 0 || (n > 0 && (!v_host || !p_host || !out_host))) return fail(CP_EINVAL, "bad arguments");
+    for (int k = 0; k < n; ++k) {
+        const uint32_t p = p_host[k];
+        if (p < 2 || p >= (1u << 31)) return fail(CP_EINVAL, "p must be in [2, 2^31)");
+        const long long lim = (long long)p * (long long)kReduceMaxCoefSum;
+        if (v_host[k] <= -lim || v_host[k] >= lim) return fail(CP_EINVAL, "|v| must be below p * 2^20");
+    }
+    if (n == 0) return CP_OK;
+    long long *v_d = nullptr;
+    uint32_t *p_d = nullptr, *o_d = nullptr;
+    int rc = dev_alloc((void **)&v_d, 8ull * n);
+    if (!rc) rc = dev_alloc((void **)&p_d, 4ull * n);
+    if (!rc) rc = dev_alloc((void **)&o_d, 4ull * n);
+    cudaError_t e = cudaSuccess;
+    if (!rc) {
+        e = cudaMemcpy(v_d, v_host, 8ull * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p_d, p_host, 4ull * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            debug_reduce_kernel<<<(n + 255) / 256, 256>>>(v_d, p_d, n, o_d);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpy(out_host, o_d, 4ull * n, cudaMemcpyDeviceToHost);
+    }
+    dev_free(v_d);
+    dev_free(p_d);
+    dev_free(o_d);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(CP_ECUDA, std::string("cp_debug_reduce: ") + cudaGetErrorString(e));
+    return CP_OK;
+}

@@ -244,7 +244,7 @@ static int launch_batch(cp_server *sv, std::vector<GatherTask> &tasks) {
     int tile_a = 0, tile_b = kGatherItems;
     uint32_t blk_a = 0, blk_b = 0;
     if (!a.empty()) {
-        tile_a = effective_tile(a, make_tile(64, kTmaRingKbDefault, 1));
+        tile_a = effective_tile(a, make_tile(64, kTmaRingKbDefault, 0));
         blk_a = assign_blocks(a, tile_a);
     }
     if (!b.empty()) blk_b = assign_blocks(b, tile_b);
@@ -277,7 +277,7 @@ extern "C" int cp_server_create(size_t mem_budget_bytes, int max_active, void *c
     sv->stream = (cudaStream_t)cuda_stream;
     sv->max_active = max_active;
     int rc;
-    if ((rc = prepare_gather_kernels())) return rc;
+    if ((rc = prepare_gather_kernels()) || (rc = crt_static_touch())) return rc;
     if ((rc = sv->arena.init(mem_budget_bytes))) return rc;
     *out = sv.release();
     return CP_OK;

@@ -87,6 +87,8 @@ struct cp_strip {
     uint32_t *scratch[2] = {nullptr, nullptr};
     uint32_t *row_out = nullptr;  // [P][D1]
     uint32_t *ones_dev = nullptr;  // P ones (the e_0 row)
+    uint32_t *crt_dev = nullptr;   // cp_read_integers: limbs, then flags, then bounds (grown on demand)
+    size_t crt_words = 0;
     GatherTask *tasks_dev = nullptr;
     int tile = kGatherItems;  // gather tile of this strip's launches
     // precomputed launches: row factors from vec[0] / vec[1], read-out chain
@@ -104,6 +106,7 @@ struct cp_strip {
         dev_free(row_out);
         dev_free(ones_dev);
         dev_free(tasks_dev);
+        dev_free(crt_dev);
     }
 };
 
@@ -214,7 +217,7 @@ extern "C" int cp_create_strip(int lattice, int L, const uint32_t *primes, int n
                                int max_rows, void *cuda_stream, cp_strip **out) {
     int rc = check_strip_args(lattice, L, primes, n_primes, max_degree, max_rows, out);
     if (rc) return rc;
-    if ((rc = prepare_gather_kernels())) return rc;
+    if ((rc = prepare_gather_kernels()) || (rc = crt_static_touch())) return rc;
     std::shared_ptr<TableSet> tabs;
     const long long D1 = max_degree >= 0 ? max_degree + 1 : (long long)L * max_rows;
     if ((rc = get_tables(lattice, L, (size_t)D1 * n_primes * 4, (cudaStream_t)cuda_stream, &tabs))) return rc;
@@ -227,7 +230,7 @@ extern "C" int cp_create_strip_potts(int lattice, int L, int v, const uint32_t *
     if (rc) return rc;
     if (v < -CP_POTTS_MAX_V || v > CP_POTTS_MAX_V) return fail(CP_EINVAL, "v must be in [-CP_POTTS_MAX_V, CP_POTTS_MAX_V]");
     if (L > CP_POTTS_MAX_L) return fail(CP_EINVAL, "L must be 1..CP_POTTS_MAX_L for the Potts strip");
-    if ((rc = prepare_gather_kernels())) return rc;
+    if ((rc = prepare_gather_kernels()) || (rc = crt_static_touch())) return rc;
     std::shared_ptr<TableSet> tabs;
     if ((rc = get_potts_tables(lattice, L, v, (cudaStream_t)cuda_stream, &tabs))) return rc;
     return make_strip(std::move(tabs), lattice, L, primes, n_primes, max_degree, max_rows, cuda_stream, out);
@@ -278,6 +281,46 @@ extern "C" int cp_read_coeffs(cp_strip *s, uint32_t *out, size_t out_len, int *h
     if ((rc = check_device_error(s->stream))) return rc;
     if (height_out) *height_out = s->height;
     return CP_OK;
+}
+
+extern "C" int cp_read_integers(cp_strip *s, uint32_t *limbs_out, size_t limbs_len, int limbs_per_coeff,
+                                uint32_t *flags_out, int *height_out) {
+    if (!s || !limbs_out) return fail(CP_EINVAL, "NULL argument");
+    const int D1 = s->D1;
+    if (limbs_per_coeff < 1 || limbs_len < (size_t)D1 * limbs_per_coeff)
+        return fail(CP_EINVAL, "limbs_len < (D+1)*limbs_per_coeff");
+    // Whitney's bound |c_j| <= C(|E|, j) of the chromatic polynomial; the Potts
+    // strip's coefficients have no such bound, only the stabilisation check
+    const bool bound = !s->tabs->potts;
+    std::vector<uint32_t> bits(D1, 0u);
+    if (bound) binomial_bits(rectangle_edges(s->lattice, s->L, s->height), D1, bits.data());
+    const size_t need = (size_t)D1 * (limbs_per_coeff + 2);
+    int rc;
+    if (need > s->crt_words) {
+        CP_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        dev_free(s->crt_dev);
+        s->crt_dev = nullptr;
+        s->crt_words = 0;
+        if ((rc = dev_alloc((void **)&s->crt_dev, need * 4))) return rc;
+        s->crt_words = need;
+    }
+    uint32_t *limbs_d = s->crt_dev, *flags_d = limbs_d + (size_t)D1 * limbs_per_coeff, *bound_d = flags_d + D1;
+    if ((rc = readout(s))) return rc;
+    CP_CUDA_TRY(cudaMemcpyAsync(bound_d, bits.data(), 4ull * D1, cudaMemcpyHostToDevice, s->stream));
+    std::vector<uint32_t> primes(s->P);
+    CP_CUDA_TRY(cudaMemcpyAsync(primes.data(), s->primes_dev, 4ull * s->P, cudaMemcpyDeviceToHost, s->stream));
+    CP_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    if ((rc = launch_crt(s->row_out, primes.data(), s->P, D1, limbs_d, limbs_per_coeff, bound ? bound_d : nullptr,
+                         flags_d, s->stream)))
+        return rc;
+    std::vector<uint32_t> flags(D1);
+    CP_CUDA_TRY(cudaMemcpyAsync(limbs_out, limbs_d, 4ull * D1 * limbs_per_coeff, cudaMemcpyDeviceToHost, s->stream));
+    CP_CUDA_TRY(cudaMemcpyAsync(flags.data(), flags_d, 4ull * D1, cudaMemcpyDeviceToHost, s->stream));
+    if ((rc = check_device_error(s->stream))) return rc;
+    if (flags_out)
+        for (int j = 0; j < D1; ++j) flags_out[j] = flags[j];
+    if (height_out) *height_out = s->height;
+    return crt_verdict(flags.data(), D1);
 }
 
 extern "C" int cp_strip_info(const cp_strip *s, uint64_t n_states[2], int *degree, int *height) {

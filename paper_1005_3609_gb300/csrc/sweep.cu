@@ -55,6 +55,9 @@ struct cp_sweep {
     int2 *rects_dev = nullptr;
     uint32_t *ptilde_dev = nullptr;  // [groups][n_rects][D1][Pg]
     uint32_t *series_dev = nullptr;  // [3][P][n]
+    uint32_t *crt_dev = nullptr;     // cp_sweep_series_integers: limbs [3][n][limbs], then flags [3][n]
+    size_t crt_words = 0;
+    std::vector<uint32_t> primes_host;
     int *err_dev = nullptr;
     GatherTask *tasks_dev = nullptr;
     std::vector<uint32_t> step_off, step_ntasks, step_blocks;
@@ -77,6 +80,7 @@ struct cp_sweep {
         dev_free(rects_dev);
         dev_free(ptilde_dev);
         dev_free(series_dev);
+        dev_free(crt_dev);
         dev_free(err_dev);
         dev_free(tasks_dev);
     }
@@ -248,7 +252,8 @@ static int sweep_build(int lattice, int k, const uint32_t *primes, int P, int ti
     sw->Pg = P / groups;
     sw->stream = stream;
     int rc;
-    if ((rc = prepare_gather_kernels())) return rc;
+    if ((rc = prepare_gather_kernels()) || (rc = crt_static_touch())) return rc;
+    sw->primes_host.assign(primes, primes + P);
     if ((rc = dev_alloc((void **)&sw->primes_dev, 4 * CP_MAX_PRIMES))) return rc;
     CP_CUDA_TRY(cudaMemcpy(sw->primes_dev, primes, 4 * P, cudaMemcpyHostToDevice));
     std::vector<uint32_t> ones(CP_MAX_PRIMES, 1u);
@@ -300,14 +305,13 @@ extern "C" int cp_sweep_create(int lattice, int k, const uint32_t *primes, int n
     if (rc) return rc;
     if (!cuda_stream) return fail(CP_EINVAL, "the sweep needs a non-default stream (graph capture)");
     {
-        const int rows = tile & 0xFFF, ring = (tile >> 12) & 0xFF, passes = (tile >> 20) & 15;
+        const int rows = tile & 0xFFF, ring = (tile >> 12) & 0xFF, edges = (tile >> 20) & 15;
         const bool reg = (rows == 1 || rows == 2 || rows == 4 || rows == 8) && (tile >> 12) == 0;
         const bool tma = (rows == 16 || rows == 32 || rows == 64 || rows == 128) && (tile >> 24) == 0 &&
-                         (ring == 0 || (ring >= 16 && ring <= 192)) &&
-                         (passes <= 2 || passes == 4 || passes == 8);
+                         (ring == 0 || (ring >= 16 && ring <= 192)) && (edges <= 2 || edges == 4);
         if (tile != 0 && !reg && !tma)
             return fail(CP_EINVAL, "tile must be 0 (autotune), 1, 2, 4, 8 (register kernel) or 16, 32, 64, 128 "
-                                   "(TMA) + (ring KB 16..192 << 12) + (chunks per thread 1, 2, 4, 8 << 20)");
+                                   "(TMA) + (ring KB 16..192 << 12) + (edges per stage 1, 2, 4 << 20)");
     }
     if (prime_groups < 0 || (prime_groups > 0 && n_primes % prime_groups != 0))
         return fail(CP_EINVAL, "prime_groups must divide n_primes");
@@ -327,8 +331,9 @@ extern "C" int cp_sweep_create(int lattice, int k, const uint32_t *primes, int n
     // launch program for each candidate tile, time one graph run (after a
     // warm-up run) and keep the fastest (tile, grouping)
     std::vector<int> tiles = tile ? std::vector<int>{tile}
-                                  : std::vector<int>{make_tile(64, 28, 1), make_tile(32, 28, 1),
-                                                     make_tile(128, 28, 1), make_tile(64, 32, 1), 4};
+                                  : std::vector<int>{make_tile(64, 32, 0), make_tile(32, 32, 0),
+                                                     make_tile(128, 32, 0), make_tile(64, 32, 1),
+                                                     make_tile(64, 32, 4), make_tile(64, 64, 0), 4};
     std::vector<int> grps;
     if (prime_groups) grps = {prime_groups};
     else
@@ -446,7 +451,39 @@ extern "C" int cp_sweep_set_primes(cp_sweep *sw, const uint32_t *primes, int n_p
     int rc = check_primes(primes, n_primes);
     if (rc) return rc;
     CP_CUDA_TRY(cudaMemcpyAsync(sw->primes_dev, primes, 4ull * n_primes, cudaMemcpyHostToDevice, sw->stream));
+    sw->primes_host.assign(primes, primes + n_primes);
     return CP_OK;
+}
+
+extern "C" int cp_sweep_series_integers(cp_sweep *sw, uint32_t *limbs_out, size_t limbs_len, int limbs_per_coeff,
+                                        uint32_t *flags_out) {
+    if (!sw || !limbs_out) return fail(CP_EINVAL, "NULL argument");
+    const int n = sw->n, P = sw->P;
+    if (limbs_per_coeff < 1 || limbs_len < 3ull * n * limbs_per_coeff)
+        return fail(CP_EINVAL, "limbs_len < 3*n_terms*limbs_per_coeff");
+    int rc;
+    const size_t need = 3ull * n * (limbs_per_coeff + 1);
+    if (need > sw->crt_words) {
+        CP_CUDA_TRY(cudaStreamSynchronize(sw->stream));
+        dev_free(sw->crt_dev);
+        sw->crt_dev = nullptr;
+        sw->crt_words = 0;
+        if ((rc = dev_alloc((void **)&sw->crt_dev, need * 4))) return rc;
+        sw->crt_words = need;
+    }
+    uint32_t *limbs_d = sw->crt_dev, *flags_d = limbs_d + 3ull * n * limbs_per_coeff;
+    for (int x = 0; x < 3; ++x)
+        if ((rc = launch_crt(sw->series_dev + (size_t)x * P * n, sw->primes_host.data(), P, n,
+                             limbs_d + (size_t)x * n * limbs_per_coeff, limbs_per_coeff, nullptr, flags_d + (size_t)x * n,
+                             sw->stream)))
+            return rc;
+    std::vector<uint32_t> flags(3ull * n);
+    CP_CUDA_TRY(cudaMemcpyAsync(limbs_out, limbs_d, 12ull * n * limbs_per_coeff, cudaMemcpyDeviceToHost, sw->stream));
+    CP_CUDA_TRY(cudaMemcpyAsync(flags.data(), flags_d, 12ull * n, cudaMemcpyDeviceToHost, sw->stream));
+    if ((rc = cp_sweep_sync(sw))) return rc;
+    if (flags_out)
+        for (size_t j = 0; j < flags.size(); ++j) flags_out[j] = flags[j];
+    return crt_verdict(flags.data(), 3 * n);
 }
 
 // The same program without the graph, with an event pair around every batched

@@ -16,6 +16,7 @@
 #include <utility>
 
 #include "cp_internal.h"
+#include "modred.cuh"
 #include "ncnnn.cuh"
 
 namespace cp {
@@ -154,7 +155,7 @@ __device__ int op_vv(Term *t, int n, int m, int i, int v) {
 }
 
 // Terms of one factor applied to one partition.
-__device__ int factor_terms(const OpDesc &op, const Labels &s, Term *t) {
+__device__ __noinline__ int factor_terms(const OpDesc &op, const Labels &s, Term *t) {
     int m = op.m, i = op.i, n = 1;
     t[0].s = s;
     t[0].coef = 1;
@@ -196,7 +197,7 @@ __device__ int factor_terms(const OpDesc &op, const Labels &s, Term *t) {
 }
 
 // Terms of a two-site table: the second factor applied to every term of the first.
-__device__ int fused_terms(const OpDesc &op, const Labels &s, Term *out) {
+__device__ __noinline__ int fused_terms(const OpDesc &op, const Labels &s, Term *out) {
     Term a[kMaxTerms];
     const int na = factor_terms(op, s, a);
     OpDesc ob = op;
@@ -507,10 +508,9 @@ static int build_table(const OpDesc &op, const RankTables *T_dev, cudaStream_t s
         cleanup();
         return fail(CP_ECUDA, std::string("table build: ") + cudaGetErrorString(e));
     }
-    // The gathers reduce sum_e coef_e x_e (x_e < p) with a float estimate of the
-    // quotient (three roundings, relative error < 2^-22), exact while the
-    // quotient's magnitude, at most sum_e |coef_e|, stays below 2^20.
-    if (herr[0] == 0 && herr[1] >= (1 << 20)) {
+    // The gathers reduce p 2^21 + sum_e coef_e x_e (x_e < p) exactly while
+    // sum_e |coef_e| into every state stays below 2^20 (modred.cuh).
+    if (herr[0] == 0 && herr[1] >= (int)kReduceMaxCoefSum) {
         cleanup();
         return fail(CP_EINVAL, "too many transitions into one state for the exact modular reduction");
     }
