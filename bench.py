@@ -309,28 +309,30 @@ def gpu_arm(args):
     updates_total = sw.updates_per_run * args.steps * world
     value = updates_total / (ms / 1e3)
 
-    # ---- e2e through the C ABI: primes host->device, series CRT'd on device, limbs device->host
+    # ---- e2e through the C ABI: primes host->device (cp_sweep_set_primes), the sweep
+    # (cp_sweep_run), the series CRT'd and checked for stability on the device and
+    # their limbs copied into a pinned host buffer (cp_sweep_series_integers)
+    import numpy as np
     pinned_primes = torch.tensor(primes, dtype=torch.int64).to(torch.int32).pin_memory()
     pinned_out = torch.zeros(3 * n * limbs, dtype=torch.int32).pin_memory()
+    out_np = pinned_out.numpy().view(np.uint32).reshape(3, n, limbs)
     h2d = 4 * P
-    d2h = 4 * 3 * n * limbs
-    for _ in range(max(1, args.warmup)):
+    d2h = 4 * 3 * n * limbs + 4 * 3 * n  # limbs and the per-term stability flags
+
+    def e2e_step():
         sw.set_primes(pinned_primes.numpy().view("uint32"))
-        step()
-        with torch.cuda.stream(stream):
-            pinned_out.copy_(limb_dev, non_blocking=True)
-        stream.synchronize()
+        sw.run()
+        return sw.series_integers(limbs_per_coeff=limbs, out=out_np)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
     for _ in range(args.steps):
-        sw.set_primes(pinned_primes.numpy().view("uint32"))
-        step()
-        with torch.cuda.stream(stream):
-            pinned_out.copy_(limb_dev, non_blocking=True)
-        stream.synchronize()
+        series = e2e_step()
     f1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -343,9 +345,6 @@ def gpu_arm(args):
         e2e_ms = float(t.item())
     e2e_value = updates_total / (e2e_ms / 1e3)
     # the e2e result must be the paper's series
-    from paper_1005_3609_gb300._lib import limbs_to_ints
-    import numpy as np
-    series = [limbs_to_ints(pinned_out.numpy().view(np.uint32).reshape(3, n, limbs)[x]) for x in range(3)]
     if dist:  # the one exchange: rank 0 gathers every rank's residues and recombines all primes
         got = shard.gather_residues(sw.read_series(), primes, dist)
         if rank == 0:
@@ -395,7 +394,9 @@ def gpu_arm(args):
                           "algorithmic_bytes_per_step": sw.site_bytes_per_run,
                           "table_bytes_per_step": sw.bytes_per_run},
                "e2e": {"value": e2e_value, "unit": "updates/s", "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps},
+                       "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms / args.steps,
+                       "path": "cp_sweep_set_primes (pinned host) -> cp_sweep_run -> cp_sweep_series_integers "
+                               "(device CRT + stability flags, limbs into pinned host memory)"},
                "gpu_launches": args.steps * (sw.launches_per_run + 3),
                "roofline": roofline,
                "hbm_gbs_algorithmic": sw.site_bytes_per_run * args.steps / (ms / 1e3) / 1e9}
@@ -423,6 +424,16 @@ def gpu_arm(args):
                                          "(one process per prime), %.1f s wall" % (args.cpu_widths, len(primes), wall)}
     if pool is not None:
         pool.close()
+    if rank == 0 and world == 1 and not args.no_extras:
+        extra = {}
+        if lattice == "square" and k == 33:
+            extra["triangular_sweep_k33"] = sweep_measure(cp, torch, "triangular", 33, primes, args)
+        p8 = primes[:8]
+        extra["config2_square_12x13"] = strip_measure(cp, torch, "square", 12, 13, p8, 5)
+        extra["config3_triangular_13x14"] = strip_measure(cp, torch, "triangular", 13, 14, p8, 5)
+        extra["serving_prefix"] = serve_measure(cp, torch, args.serve_prefix, args.serve_budget_gb,
+                                                args.serve_max_active)
+        out["extra_workloads"] = extra
     if rank == 0:
         print(json.dumps(out))
     if dist:
@@ -484,12 +495,11 @@ def pct(xs, q):
     return xs[min(len(xs) - 1, int(round(q / 100.0 * (len(xs) - 1))))]
 
 
-def serve_arm(args):
-    import torch
-    import paper_1005_3609_gb300 as cp
-    torch.cuda.set_device(0)
-    cp.load()
-    reqs = synthetic_inputs.serving_requests(seed=1, rate_per_s=200.0, n=10000)[: args.serve_n]
+def serve_measure(cp, torch, n_req, budget_gb, max_active, with_plain=True):
+    """Serve the first n_req requests of the serving stream (seed 1, 200 req/s offered) in real
+    time, then the same requests at 0.7x the measured capacity, then (with_plain) one
+    (rectangle, prime) at a time.  Returns the measurement as a dict."""
+    reqs = synthetic_inputs.serving_requests(seed=1, rate_per_s=200.0, n=10000)[:n_req]
     pcache = {}
 
     def primes_of(r):
@@ -502,8 +512,8 @@ def serve_arm(args):
     for r in reqs:
         primes_of(r)
     stream = torch.cuda.Stream()
-    budget = int(args.serve_budget_gb * (1 << 30))
-    with cp.Server(budget, max_active=args.serve_max_active, stream=stream) as sv:
+    budget = int(budget_gb * (1 << 30))
+    with cp.Server(budget, max_active=max_active, stream=stream) as sv:
         # warm-up: tables of every (lattice, width) in the stream, one tiny request each
         for lat in ("square", "triangular"):
             for L in sorted({r["L"] for r in reqs}):
@@ -513,7 +523,7 @@ def serve_arm(args):
                 sv.release(rid)
         sv.poll()
         st0 = sv.stats()
-        clocks = ClockSampler(0)
+        clocks = ClockSampler(torch.cuda.current_device())
         clocks.start()
         lat, wall = serve_stream(cp, sv, reqs, primes_of)
         clk = clocks.stop()
@@ -523,34 +533,207 @@ def serve_arm(args):
         # supplementary stream at 0.7x the measured capacity (added; arrival times rescaled)
         scale = 0.7 * cap_rps / 200.0
         lat07, wall07 = serve_stream(cp, sv, reqs, primes_of, rate_scale=scale)
-    # plain: the same requests one (rectangle, prime) at a time
-    t = time.perf_counter()
-    upd_plain = 0
-    for r in reqs:
-        for p in primes_of(r):
-            with cp.Strip(r["lattice"], r["L"], [p], max_degree=-1, max_rows=r["N"], stream=stream) as s:
-                s.advance(r["N"] - 1)
-                s.read()
-    plain_s = time.perf_counter() - t
-    out = {"metric": "served rectangle solves: state-coeff updates/s and p50/p99 latency", "value": upd / wall,
-           "unit": "updates/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": wall * 1e3,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-           "config": {"workload": "serving: Poisson stream seed 1, 200 req/s offered, first %d of 10000 requests; "
-                                  "lattice U{square, triangular}, L U{4..16}, N in {L, L+1}, 4..16 primes, full degree"
-                                  % len(reqs),
-                      "mem_budget_gb": args.serve_budget_gb, "max_active": args.serve_max_active},
-           "requests_per_s": cap_rps,
+    out = {"requests": len(reqs), "updates_per_s": upd / wall, "wall_s": wall, "requests_per_s": cap_rps,
            "server_steps": st1["steps"] - st0["steps"], "gpu_launches": st1["launches"] - st0["launches"],
            "latency_s": {"p50": pct([x[2] for x in lat], 50), "p99": pct([x[2] for x in lat], 99),
                          "queue_p50": pct([x[0] for x in lat], 50), "queue_p99": pct([x[0] for x in lat], 99),
-                         "service_p50": pct([x[1] for x in lat], 50), "service_p99": pct([x[1] for x in lat], 99)},
+                         "service_p50": pct([x[1] for x in lat], 50), "service_p99": pct([x[1] for x in lat], 99),
+                         "note": "offered 200 req/s is several times the capacity: p50/p99 at saturation are "
+                                 "mostly queueing; the 0.7x stream shows the latency below saturation"},
            "at_0.7x_capacity (added)": {"offered_req_per_s": 200.0 * scale, "wall_s": wall07,
                                         "p50": pct([x[2] for x in lat07], 50), "p99": pct([x[2] for x in lat07], 99),
-                                        "queue_p99": pct([x[0] for x in lat07], 99)},
-           "served_vs_plain": {"served_s": wall, "plain_s": plain_s, "speedup": plain_s / wall,
-                               "plain": "each request one prime at a time, 1-prime strip, per-site launches"}}
+                                        "queue_p99": pct([x[0] for x in lat07], 99)}}
+    if with_plain:
+        t = time.perf_counter()
+        for r in reqs:
+            for p in primes_of(r):
+                with cp.Strip(r["lattice"], r["L"], [p], max_degree=-1, max_rows=r["N"], stream=stream) as st:
+                    st.advance(r["N"] - 1)
+                    st.read()
+        plain_s = time.perf_counter() - t
+        out["served_vs_plain"] = {"served_s": wall, "plain_s": plain_s, "speedup": plain_s / wall,
+                                  "plain": "each request one prime at a time, 1-prime strip, per-site launches"}
     if clk:
         out["clocks"] = clk
+    return out
+
+
+def serve_arm(args):
+    import torch
+    import paper_1005_3609_gb300 as cp
+    torch.cuda.set_device(0)
+    cp.load()
+    m = serve_measure(cp, torch, args.serve_n, args.serve_budget_gb, args.serve_max_active)
+    out = {"metric": "served rectangle solves: state-coeff updates/s and p50/p99 latency", "value": m["updates_per_s"],
+           "unit": "updates/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": m["wall_s"] * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+           "config": {"workload": "serving: Poisson stream seed 1, 200 req/s offered, first %d of 10000 requests; "
+                                  "lattice U{square, triangular}, L U{4..16}, N in {L, L+1}, 4..16 primes, full degree"
+                                  % m["requests"],
+                      "mem_budget_gb": args.serve_budget_gb, "max_active": args.serve_max_active}}
+    out.update({k: v for k, v in m.items() if k not in ("updates_per_s", "wall_s")})
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------- further workloads on the default line
+
+def baxter_bulk(n):
+    """Baxter's product for the triangular lattice's (1-x)^2 exp(f_b)/q, eq. (efb), to x^(n-1)."""
+    ser = [1] + [0] * (n - 1)
+
+    def mul_factor(e, power):  # ser *= (1 - x^e)^power
+        for _ in range(abs(power)):
+            if power > 0:
+                for i in range(n - 1, e - 1, -1):
+                    ser[i] -= ser[i - e]
+            else:
+                for i in range(e, n):
+                    ser[i] += ser[i - e]
+
+    for j in range(1, n):
+        for e, pw in ((6 * j - 3, 1), (6 * j - 2, 2), (6 * j - 1, 1), (6 * j - 5, -1), (6 * j - 4, -1),
+                      (6 * j, -1), (6 * j + 1, -1)):
+            if e < n:
+                mul_factor(e, pw)
+    return ser
+
+
+def triangular_printed():
+    s, c = [], []
+    for ln in open(os.path.join(ROOT, "tests", "golden", "triangular_series.txt")):
+        if ln.startswith("#") or not ln.strip():
+            continue
+        f = ln.split()
+        s.append(int(f[1]))
+        c.append(int(f[2]))
+    return s, c
+
+
+def sweep_measure(cp, torch, lattice, k, primes, args):
+    """One more batched sweep (tables built and tile autotuned before timing): ms per sweep,
+    updates/s, the gather's roofline fractions and the check against the printed series."""
+    stream = torch.cuda.Stream()
+    sw = cp.Sweep(lattice, k, primes, stream, tile=0, prime_groups=0)
+    for _ in range(args.warmup):
+        sw.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sw.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    series = sw.series_integers()
+    gather_ms, n_gather, _ = sw.profile()
+    peak = (load_peaks() or {}).get("hbm_gbs") or 6800.0
+    n = sw.n_terms
+    out = {"workload": "%s lattice finite-lattice sweep k=%d, %d rectangles, %d primes, P~ to w^%d"
+                       % (lattice, k, sw.n_rects, len(primes), n - 1),
+           "ms_per_sweep": ms, "updates_per_s": sw.updates_per_run / (ms / 1e3),
+           "tile": tile_name(sw.tile), "prime_groups": sw.prime_groups,
+           "gather_roofline_frac": round(sw.site_bytes_per_run / (gather_ms / 1e3) / 1e9 / peak, 4),
+           "gather_roofline_frac_tables_own_bytes": round(sw.bytes_per_run / (gather_ms / 1e3) / 1e9 / peak, 4),
+           "gather_launches": n_gather, "gather_ms": gather_ms}
+    if lattice == "triangular":
+        surf, corner = triangular_printed()
+        out["check"] = {"bulk_equals_baxter_product": series[0] == baxter_bulk(n),
+                        "surface_corner_match_printed": series[1] == surf[:n] and series[2] == corner[:n]}
+    sw.close()
+    return out
+
+
+def strip_measure(cp, torch, lattice, L, N, primes, reps):
+    """One plain rectangle solve at full degree (a strip reset to e_0, N-1 rows, read-out)."""
+    stream = torch.cuda.Stream()
+    with cp.Strip(lattice, L, primes, max_degree=-1, max_rows=N, stream=stream) as s:
+        row_upd, _, ro_upd, _, _, _ = s.work()
+        out_dev = torch.zeros(len(primes) * L * N, dtype=torch.int32, device="cuda")
+
+        def once():
+            s.reset()
+            s.advance(N - 1)
+            s.read_device(out_dev.data_ptr(), out_dev.numel())
+
+        once()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            once()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        upd = (N - 1) * row_upd + ro_upd
+        ints = s.read_integers(strict=False)
+    return {"workload": "%s %dx%d, full degree %d, %d primes: reset, %d rows, read-out" % (
+                lattice, L, N, L * N - 1, len(primes), N - 1),
+            "ms_per_solve": ms, "updates_per_s": upd / (ms / 1e3), "updates": upd,
+            "exact_integers_from_these_primes": ints[2] == 0}
+
+
+# ---------------------------------------------------------------- paper-scale workload
+
+def paper_arm(args):
+    """The paper's own scale: k = 41 (widths up to m_max = 20, Sec. 4.2-4.3) on 16 primes,
+    as two prime groups of 8 swept back to back (8 primes of width-20 vectors take about
+    250 GB, so both groups do not fit at once); the 16 primes' series residues are then
+    recombined by CRT with the stabilisation check (cp_crt_checked)."""
+    import numpy as np
+    import torch
+    import paper_1005_3609_gb300 as cp
+    torch.cuda.set_device(0)
+    lattice, k = args.lattice, 41
+    primes = cp.select_primes(synthetic_inputs.prime_draws(0, 128), 16)
+    stream = torch.cuda.Stream()
+    tile = args.tile or (64 | (32 << 12))
+    table_layout(cp, args)
+    peak = (load_peaks() or {}).get("hbm_gbs") or 6800.0
+    groups, res_all = [], []
+    for g in range(2):
+        pg = primes[8 * g: 8 * g + 8]
+        t0 = time.perf_counter()
+        sw = cp.Sweep(lattice, k, pg, stream, tile=tile, prime_groups=1)
+        setup_s = time.perf_counter() - t0
+        for _ in range(max(1, args.warmup)):
+            sw.run()
+        sw.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sw.run()
+        e1.record(stream)
+        sw.sync()
+        ms = e0.elapsed_time(e1)
+        res_all.append(sw.read_series())
+        groups.append({"primes": pg, "ms": ms, "setup_s": setup_s, "updates": sw.updates_per_run,
+                       "updates_per_s": sw.updates_per_run / (ms / 1e3),
+                       "frac_per_update_bytes": round(sw.site_bytes_per_run / (ms / 1e3) / 1e9 / peak, 4),
+                       "frac_tables_own_bytes": round(sw.bytes_per_run / (ms / 1e3) / 1e9 / peak, 4)})
+        n = sw.n_terms
+        sw.close()
+    series, stable = [], True
+    for x in range(3):
+        ints, _, rc = cp.crt_checked(np.concatenate([res_all[0][x], res_all[1][x]], axis=0), primes)
+        series.append(ints)
+        stable = stable and rc == 0
+    check = {"series_stable_over_16_primes": stable}
+    if lattice == "square":
+        t = table1()
+        check["series_match_table1"] = (series[0] == t["alpha"][:n] and series[1] == t["beta"][:n]
+                                        and series[2][: n - 1] == t["gamma"][: n - 1])
+    else:
+        surf, corner = triangular_printed()
+        check["bulk_equals_baxter_product"] = series[0] == baxter_bulk(n)
+        check["surface_corner_match_printed"] = series[1] == surf[:n] and series[2] == corner[:n]
+    tot_ms = sum(g_["ms"] for g_ in groups)
+    upd = sum(g_["updates"] for g_ in groups)
+    out = {"metric": "state-coeff updates/s (paper-scale finite-lattice sweep)", "value": upd / (tot_ms / 1e3),
+           "unit": "updates/s", "n_gpus": 1, "steps": 1, "warmup": max(1, args.warmup), "ms_per_step": tot_ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+           "config": {"workload": "%s lattice finite-lattice sweep k=41 (widths 1..20), 16 primes as two groups "
+                                  "of 8 swept back to back, series CRT'd over all 16" % lattice,
+                      "tile": tile_name(tile)},
+           "groups": groups, "check": check}
     print(json.dumps(out))
 
 
@@ -718,7 +901,7 @@ def main():
     ap.add_argument("--cpu-widths", type=int, default=13, help="widths of the CPU-baseline sample")
     ap.add_argument("--ref-widths", type=int, default=11, help="widths of each reference-arm step")
     ap.add_argument("--no-plain", action="store_true")
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "serve", "probe"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "serve", "probe", "paper"])
     ap.add_argument("--probe-L", type=int, default=18, help="strip width of the probe workload")
     ap.add_argument("--probe-D", type=int, default=62)
     ap.add_argument("--probe-rows", type=int, default=4)
@@ -727,6 +910,10 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=150.0)
     ap.add_argument("--serve-max-active", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the further workloads of the default line (triangular sweep, configs 2/3, serving)")
+    ap.add_argument("--serve-prefix", type=int, default=100,
+                    help="requests of the serving stream run on the default line")
     ap.add_argument("--per-site-tables", action="store_true",
                     help="one table per site factor instead of two-site tables (same results)")
     args = ap.parse_args()
@@ -736,6 +923,8 @@ def main():
         serve_arm(args)
     elif args.workload == "probe":
         probe_arm(args)
+    elif args.workload == "paper":
+        paper_arm(args)
     else:
         gpu_arm(args)
 

@@ -414,6 +414,17 @@ int cp_debug_wait_timeout(long long cycles);
  * otherwise.  Synchronous. */
 int cp_debug_reduce(const int64_t *v_host, const uint32_t *p_host, int n, uint32_t *out_host);
 
+/* One chromatic transfer-matrix table as the kernels use it (CSR by
+ * destination): paired = 1 for the square lattice's two-site tables; which = 0
+ * for the row factors (index 0 = T_1, or T_2 T_1 when paired), 1 for the
+ * read-out chain.  info[0..3] = source states, destination states, non-zeros,
+ * source bits of the packed edge (src | shift << bits | coef << (bits + 2),
+ * coef in two's complement).  row_ptr_host (max_rows >= destinations + 1) and
+ * edges_host (max_edges >= non-zeros) may be NULL to query info only.  Builds
+ * the tables on the current device if needed. */
+int cp_debug_table(int lattice, int L, int paired, int which, int index, uint32_t *row_ptr_host, uint64_t max_rows,
+                   uint32_t *edges_host, uint64_t max_edges, uint64_t info[4]);
+
 /* Partitions of the space in rank order, as canonical labels:
  * out_host[r*m + i] = block label of site i (first-occurrence order).
  * Errors: CP_EINVAL if the space has more than max_states states. */

@@ -71,6 +71,8 @@ SIGNATURES = {
     "cp_server_poll": (ctypes.c_int, [vp, u64p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
     "cp_server_cancel": (ctypes.c_int, [vp, ctypes.c_uint64]),
     "cp_debug_wait_timeout": (ctypes.c_int, [ctypes.c_longlong]),
+    "cp_debug_table": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, u32p,
+                                      ctypes.c_uint64, u32p, ctypes.c_uint64, u64p]),
     "cp_debug_reduce": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64), u32p, ctypes.c_int, u32p]),
     "cp_server_stats": (ctypes.c_int, [vp, u64p, u64p, u64p, ctypes.POINTER(ctypes.c_size_t)]),
     "cp_server_destroy": (None, [vp]),
@@ -306,6 +308,20 @@ def debug_reduce(values, primes):
     check("cp_debug_reduce", load().cp_debug_reduce(v.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), pp, len(v),
                                                     out.ctypes.data_as(u32p)))
     return [int(x) for x in out]
+
+
+def debug_table(lattice, L, paired, which, index):
+    """(row_ptr, edges, (n_src, n_dst, nnz, src_bits)) of one table (cp_debug_table)."""
+    info = (ctypes.c_uint64 * 4)()
+    check("cp_debug_table", load().cp_debug_table(lattice_id(lattice), L, paired, which, index, None, 0, None, 0,
+                                                  info))
+    n_src, n_dst, nnz, sb = (int(x) for x in info)
+    rp = np.zeros(n_dst + 1, dtype=np.uint32)
+    ed = np.zeros(max(nnz, 1), dtype=np.uint32)
+    check("cp_debug_table", load().cp_debug_table(lattice_id(lattice), L, paired, which, index,
+                                                  rp.ctypes.data_as(u32p), rp.size, ed.ctypes.data_as(u32p), ed.size,
+                                                  info))
+    return rp, ed[:nnz], (n_src, n_dst, nnz, sb)
 
 
 def debug_enumerate_space(kind, m, e=0, max_states=1 << 22):

@@ -376,7 +376,16 @@ namespace cp {
 int debug_wait_timeout(long long cycles, cudaStream_t st);
 int check_space(int kind, int m, int e, uint64_t *n_bad, uint64_t *size);
 int enumerate_space(int kind, int m, int e, uint8_t *out_host, uint64_t max_states, uint64_t *size);
+int debug_table(int lattice, int L, int paired, int which, int index, uint32_t *row_ptr_host, uint64_t max_rows,
+                uint32_t *edges_host, uint64_t max_edges, uint64_t info[4]);
 }  // namespace cp
+
+extern "C" int cp_debug_table(int lattice, int L, int paired, int which, int index, uint32_t *row_ptr_host,
+                              uint64_t max_rows, uint32_t *edges_host, uint64_t max_edges, uint64_t info[4]) {
+    if ((lattice != CP_SQUARE && lattice != CP_TRIANGULAR) || L < 1 || L > CP_MAX_L || (which != 0 && which != 1))
+        return fail(CP_EINVAL, "bad table");
+    return debug_table(lattice, L, paired, which, index, row_ptr_host, max_rows, edges_host, max_edges, info);
+}
 
 extern "C" int cp_debug_check_space(int kind, int m, int e, uint64_t *n_bad, uint64_t *size) {
     if (m < 1 || m > CP_MAX_L || kind < 0 || kind > 2 || (kind == 1 && (e < 0 || e + 1 >= m)) ||

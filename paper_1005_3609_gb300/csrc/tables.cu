@@ -781,6 +781,34 @@ int get_potts_tables(int lattice, int L, int v, cudaStream_t st, std::shared_ptr
     return CP_OK;
 }
 
+// Copy one cached (or freshly built) chromatic table to the host.
+int debug_table(int lattice, int L, int paired, int which, int index, uint32_t *row_ptr_host, uint64_t max_rows,
+                uint32_t *edges_host, uint64_t max_edges, uint64_t info[4]) {
+    const int old = set_factor_pairing(paired ? 2 : 0);
+    std::shared_ptr<TableSet> ts;
+    int rc = get_tables(lattice, L, 0, 0, &ts);
+    set_factor_pairing(old);
+    if (rc) return rc;
+    const std::vector<SiteTable> &v = which ? ts->last : ts->row;
+    if (index < 0 || index >= (int)v.size()) return fail(CP_EINVAL, "table index out of range");
+    const SiteTable &t = v[index];
+    if (info) {
+        info[0] = t.n_src;
+        info[1] = t.n_dst;
+        info[2] = t.nnz;
+        info[3] = (uint64_t)t.op.src_bits;
+    }
+    if (row_ptr_host) {
+        if (max_rows < t.n_dst + 1) return fail(CP_EINVAL, "max_rows < n_dst + 1");
+        CP_CUDA_TRY(cudaMemcpy(row_ptr_host, t.row_ptr, 4 * (t.n_dst + 1), cudaMemcpyDeviceToHost));
+    }
+    if (edges_host) {
+        if (max_edges < t.nnz) return fail(CP_EINVAL, "max_edges < nnz");
+        CP_CUDA_TRY(cudaMemcpy(edges_host, t.edges, 4 * t.nnz, cudaMemcpyDeviceToHost));
+    }
+    return CP_OK;
+}
+
 void clear_table_cache() {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     for (auto &c : g_cache) c.clear();  // strips keep their own shared_ptr alive

@@ -86,3 +86,12 @@ def test_newer_entry_points_validate_without_gpu(lib):
     assert old in (0, 1, 2)
     assert lib.cp_set_factor_pairing(7) == 0
     assert lib.cp_set_factor_pairing(old) == 2
+
+
+def test_whitney_bits_on_host(lib):
+    import math
+    from paper_1005_3609_gb300 import _lib
+    for lattice, L, N in (("square", 12, 13), ("triangular", 13, 14), ("square", 1, 1), ("square", 3, 1)):
+        e = L * (N - 1) + N * (L - 1) + ((L - 1) * (N - 1) if lattice == "triangular" else 0)
+        n = L * N + 3
+        assert _lib.whitney_bits(lattice, L, N, n) == [math.comb(e, j).bit_length() for j in range(n)]

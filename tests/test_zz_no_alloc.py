@@ -65,3 +65,35 @@ def test_static_crt_rejects_oversize(lib):
     rc, _ = call(lib, "cp_crt_static", res, primes, 17)
     assert rc == -1  # CP_EINVAL
     assert b"CP_CRT_STATIC_BYTES" in lib.cp_last_error()
+
+
+FRESH = r"""
+import sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+sys.path.insert(0, sys.argv[1] + "/tests")
+import gpu_util
+from paper_1005_3609_gb300 import _lib
+lib = _lib.load()
+primes = gpu_util.seed_primes(6, seed=4)
+rng = np.random.default_rng(3)
+res = np.stack([rng.integers(0, p, size=4096, dtype=np.int64) for p in primes]).astype(np.uint32)
+out = []
+for fn in ("cp_crt_static", "cp_crt"):  # the allocation-free call comes first in this process
+    o = np.zeros((res.shape[1], 7), dtype=np.uint32)
+    rc = getattr(lib, fn)(res.ctypes.data_as(_lib.u32p), np.asarray(primes, dtype=np.uint32).ctypes.data_as(_lib.u32p),
+                          len(primes), res.shape[1], o.ctypes.data_as(_lib.u32p), 7)
+    assert rc == 0, (fn, lib.cp_last_error())
+    out.append(o)
+assert np.array_equal(out[0], out[1])
+print("fresh ok")
+"""
+
+
+def test_static_crt_first_call_in_a_fresh_process(lib):
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", FRESH, root], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "fresh ok" in r.stdout, r.stdout + r.stderr
