@@ -265,9 +265,10 @@ typedef struct cp_sweep cp_sweep;
 
 /* tile: 0 = autotune; 1, 2, 4, 8 = register gather kernel, rows per warp;
  *       16, 32, 64, 128 = TMA gather kernel, rows per block, optionally plus
- *       (ring KB << 12) with ring KB in 16..192 (shared-memory ring size, 0 =
- *       28 KB: seven blocks per SM) and
- *       (chunks per consumer thread << 20) with 1, 2, 4 or 8;
+ *       (ring KB << 12) with ring KB in 16..192 (shared-memory ring per block,
+ *       0 = 48 KB: four blocks per SM; raised to hold two stages) and
+ *       (edges per stage << 20) with 1, 2, 4 or 8 (0 = about 16 KB of source
+ *       rows per stage);
  * prime_groups: number of strips per width, dividing n_primes, or 0 = autotune.
  * cuda_stream must be a non-default stream (the program is graph-captured on it).
  * Errors: CP_EINVAL (k < 4, k/2 > CP_MAX_L, series longer than 128 terms, bad

@@ -169,9 +169,9 @@ void append_gather_tasks(std::vector<GatherTask> *tasks, const SiteTable &tab, c
 // Gather tile (low 12 bits): 1, 2, 4, 8 = register kernel with that many rows
 // per warp (8 warps per block); 16, 32, 64, 128 = TMA kernel with that many rows
 // per block.  For TMA tiles, bits 12..19 = ring size in KB (0: default) and
-// bits 20..23 = edges per stage, 1, 2 or 4 (0: picked from the row size).  A
+// bits 20..23 = edges per stage, 1, 2, 4 or 8 (0: picked from the row size).  A
 // batch whose rows are not all 16-byte chunked uses the register kernel.
-constexpr int kTmaRingKbDefault = 32;
+constexpr int kTmaRingKbDefault = 48;
 inline int make_tile(int rows, int ring_kb, int edges = 0) { return rows | (ring_kb << 12) | (edges << 20); }
 inline int tile_edges(int tile) { return (tile >> 20) & 15; }
 inline int tile_ring_kb(int tile) { int r = (tile >> 12) & 0xFF; return r ? r : kTmaRingKbDefault; }

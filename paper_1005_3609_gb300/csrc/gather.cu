@@ -144,21 +144,25 @@ uint32_t task_blocks(const GatherTask &t, int items) {
     return (t.rows + per - 1) / per;
 }
 
-// For TMA tiles: edges per stage (bits 20..23) default to about 8 KB of rows per
+// For TMA tiles: edges per stage (bits 20..23) default to about 16 KB of rows per
 // stage, and the ring is raised to hold at least two stages of the widest row
 // group; a batch the TMA kernel cannot take uses the register kernel.
 int effective_tile(const std::vector<GatherTask> &tasks, int items) {
     if (!tile_is_tma(items)) return items & 0xFFF;
-    uint32_t max_rb = 0;
+    uint32_t max_rb = 0, max_g = 1;
     for (auto &t : tasks) {
         if (!tma_usable(t)) return kGatherItems;
         max_rb = std::max(max_rb, t.cw * 16u);
+        uint32_t G = 1;  // row groups of the kernel's blocks (G * cw <= 256)
+        while (G < 8 && 2 * G * t.cw <= 256) G *= 2;
+        max_g = std::max(max_g, G);
     }
     int edges = tile_edges(items);
-    if (edges != 1 && edges != 2 && edges != 4) {
-        const uint32_t per = max_rb ? 8192u / max_rb : 4u;
-        edges = per >= 4 ? 4 : (per >= 2 ? 2 : 1);
+    if (edges != 1 && edges != 2 && edges != 4 && edges != 8) {
+        const uint32_t per = max_rb ? 16384u / max_rb : 8u;
+        edges = per >= 8 ? 8 : (per >= 4 ? 4 : (per >= 2 ? 2 : 1));
     }
+    while ((uint32_t)edges * max_g > 32) edges /= 2;  // the producer warp has one lane per group and slot
     int ring = (items >> 12) & 0xFF;
     if (!ring) ring = kTmaRingKbDefault;
     // a row group spans at most 4 KB of slot (G rows of cw chunks, G cw <= 256): two stages need 8 KB per edge
@@ -251,7 +255,8 @@ int check_device_error(cudaStream_t st) {
     CP_CUDA_TRY(cudaMemcpy(&h, f, sizeof(int), cudaMemcpyDeviceToHost));
     if (h) {
         CP_CUDA_TRY(cudaMemset(f, 0, sizeof(int)));
-        return fail(CP_ETIMEOUT, "a bounded wait in the TMA gather kernel ran out (flags " + std::to_string(h) + ")");
+        return fail(CP_ETIMEOUT, "a bounded wait in the TMA gather kernel ran out, or a block refused its "
+                                 "configuration (flags " + std::to_string(h) + ")");
     }
     return CP_OK;
 }

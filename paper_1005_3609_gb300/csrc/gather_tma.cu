@@ -86,11 +86,12 @@ __device__ __forceinline__ uint32_t fast_div_u(uint32_t x, uint32_t magic) { ret
 // Shared state of one block.
 struct TmaShared {
     uint64_t full_bar[kTmaMaxSlots], empty_bar[kTmaMaxSlots];  // per stage (at most one stage per slot)
-    int cf[kTmaMaxSlots];                                       // coefficient of the edge in each slot
-    uint32_t sh[kTmaMaxSlots];                                  // its shift (degrees)
-    uint32_t rp[kTmaMaxRows + 1];                               // the block's row pointers
+    int cf[kTmaMaxSlots];          // per slot: the edge's coefficient
+    uint32_t sh[kTmaMaxSlots];     // per slot: the edge's shift (degrees)
+    uint32_t rp[kTmaMaxRows + 1];  // the block's row pointers
     uint32_t p[CP_MAX_PRIMES], m[CP_MAX_PRIMES], s[CP_MAX_PRIMES];  // reduction constants per prime
-    long long deadline;                                         // clock64 limit of every wait
+    long long deadline;            // clock64 limit of every wait
+    GatherTask task;               // the block's task (read where needed, not held in registers)
     int abort_flag;
 };
 
@@ -99,30 +100,40 @@ struct TmaBlock {
     uint32_t row0, nrows, G, NS, act;
 };
 
+__device__ __forceinline__ void tma_group_rows(const TmaBlock &bk, uint32_t g, uint32_t *r0, uint32_t *r1) {
+    *r0 = bk.nrows * g / bk.G;
+    *r1 = bk.nrows * (g + 1) / bk.G;
+}
+
 // ---------------------------------------------------------------- producer
-// Stages of a group: its rows in order, ceil(edges / E) stages per row (rows
-// without edges have none), so a stage never holds edges of two rows; the
-// slots of a row's last stage that have no edge carry coefficient 0.
+// Stages of a group: its edges in CSR order, E per stage (the last stage of the
+// group may be partly empty: coefficient 0, no copy).  Stages are not aligned
+// to destination rows; the consumers find the row ends from the row pointers.
 template <int E>
 __device__ __forceinline__ void tma_produce(const GatherTask &t, const TmaBlock &bk, TmaShared &S, uint8_t *ring,
                                             int *err) {
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t g = lane / E, j = lane - g * E;  // lane j of group g's stages
+    const uint32_t g = lane / E, j = lane - g * E;  // lane j of group g's stages (G * E <= 32)
     const bool has = g < bk.G;
-    const uint32_t r1 = has ? bk.nrows * (g + 1) / bk.G : 0u;
-    uint32_t r = has ? bk.nrows * g / bk.G : 0u;
-    while (r < r1 && S.rp[r + 1] == S.rp[r]) ++r;  // first row with edges
-    uint32_t e = r < r1 ? S.rp[r] : 0u, re = r < r1 ? S.rp[r + 1] : 0u;  // this stage's first edge, row end
-    uint32_t q = (r < r1 && e + j < re) ? __ldg(t.edges + e + j) : 0u;
+    uint32_t r0 = 0, r1 = 0, gb = 0, gn = 0;
+    if (has) {
+        tma_group_rows(bk, g, &r0, &r1);
+        gb = S.rp[r0];
+        gn = S.rp[r1] - gb;
+    }
+    const uint32_t kmax = __reduce_max_sync(0xffffffffu, has ? (gn + E - 1) / E : 0u);
     const uint32_t RB = t.cw * 16u;
     const uint8_t *in_bytes = reinterpret_cast<const uint8_t *>(t.in);
     const size_t src_row_bytes = (size_t)t.C * 16u;
     const uint32_t src_mask = (1u << t.src_bits) - 1u;
     const long long deadline = S.deadline;
+    uint32_t q = (has && j < gn) ? __ldg(t.edges + gb + j) : 0u;
     uint32_t s = 0, ph = 0;
-    for (uint32_t k = 0; __any_sync(0xffffffffu, r < r1); ++k) {
+    for (uint32_t k = 0; k < kmax; ++k) {
+        const uint32_t idx = k * E + j;  // edge within the group
+        const uint32_t qn = (has && idx + E < gn) ? __ldg(t.edges + gb + idx + E) : 0u;  // next stage's edge
         bool lok = true;
-        if (r < r1) {
+        if (has && k * E < gn) {  // the group has a stage k
             const uint32_t st = g * bk.NS + s;
             if (k >= bk.NS && !mbar_wait(smem_addr(&S.empty_bar[st]), ph ^ 1u, deadline)) {
                 atomicOr(err, 2);
@@ -131,7 +142,7 @@ __device__ __forceinline__ void tma_produce(const GatherTask &t, const TmaBlock 
             if (lok) {
                 const uint32_t fb = smem_addr(&S.full_bar[st]);
                 const uint32_t slot = st * E + j;
-                if (e + j < re) {
+                if (idx < gn) {
                     const uint32_t sh = (q >> t.src_bits) & 3u;
                     S.cf[slot] = (int)q >> (t.src_bits + 2);
                     S.sh[slot] = sh;
@@ -147,55 +158,31 @@ __device__ __forceinline__ void tma_produce(const GatherTask &t, const TmaBlock 
                     } else {
                         mbar_arrive(fb);
                     }
-                } else {  // past the row's last edge: a slot that adds nothing
+                } else {  // past the group's last edge: a slot that adds nothing
                     S.cf[slot] = 0;
                     S.sh[slot] = 0;
                     mbar_arrive(fb);
                 }
-                // next stage of the group: the rest of this row, or the next row with edges
-                e += E;
-                if (e >= re) {
-                    ++r;
-                    while (r < r1 && S.rp[r + 1] == S.rp[r]) ++r;
-                    if (r < r1) {
-                        e = S.rp[r];
-                        re = S.rp[r + 1];
-                    }
-                }
-                q = (r < r1 && e + j < re) ? __ldg(t.edges + e + j) : 0u;
             }
         }
         if (!__all_sync(0xffffffffu, lok)) break;
+        q = qn;
         if (++s == bk.NS) {
             s = 0;
             ph ^= 1u;
         }
     }
-}
-
-// Total stages of group g (rows in order, ceil(edges / E) each).
-template <int E>
-__device__ __forceinline__ uint32_t tma_group_stages(const TmaBlock &bk, const TmaShared &S, uint32_t g) {
-    const uint32_t r0 = bk.nrows * g / bk.G, r1 = bk.nrows * (g + 1) / bk.G;
-    uint32_t n = 0;
-    for (uint32_t r = r0; r < r1; ++r) n += (S.rp[r + 1] - S.rp[r] + E - 1) / E;
-    return n;
-}
-
-// The producer does not leave while copies it issued may be in flight: one lane
-// per group waits (bounded) for the group's last NS stages to have landed.
-template <int E>
-__device__ __forceinline__ void tma_drain(const TmaBlock &bk, TmaShared &S, int *err) {
-    const uint32_t lane = threadIdx.x & 31;
-    if (lane >= bk.G) return;
-    const uint32_t kg = tma_group_stages<E>(bk, S, lane);
-    const uint32_t last = min(kg, bk.NS);
-    for (uint32_t i = 0; i < last; ++i) {
-        const uint32_t k = kg - 1 - i;
-        if (!mbar_wait(smem_addr(&S.full_bar[lane * bk.NS + k % bk.NS]), (k / bk.NS) & 1u,
-                       S.deadline + kWaitCycles)) {
-            atomicOr(err, 4);
-            return;
+    // do not leave while own copies are in flight: one lane per group waits
+    // (bounded) for the group's last NS stages to have landed
+    if (has && j == 0) {
+        const uint32_t kg = (gn + E - 1) / E;
+        const uint32_t last = min(kg, bk.NS);
+        for (uint32_t i = 0; i < last; ++i) {
+            const uint32_t k = kg - 1 - i;
+            if (!mbar_wait(smem_addr(&S.full_bar[g * bk.NS + k % bk.NS]), (k / bk.NS) & 1u, deadline + kWaitCycles)) {
+                atomicOr(err, 4);
+                return;
+            }
         }
     }
 }
@@ -207,6 +194,9 @@ __device__ __forceinline__ uint4 lds128(uint32_t addr) {
 }
 
 // ---------------------------------------------------------------- consumers
+// Per stage: load the E chunks and coefficients into registers, release the
+// stage, then accumulate edge by edge; after the last edge of a row (and for
+// the empty rows that follow it) reduce the four words and store them.
 // PRED: the warp holds chunks of degree < kTmaMaxShift, where a shifted copy
 // leaves the slot's low chunks unwritten and the shift must be checked.
 template <int E, bool PRED>
@@ -217,58 +207,72 @@ __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock 
     const uint32_t gc = t.c0 + c;  // chunk within the row
     const uint32_t deg = fast_div_u(gc, t.magic_cpd);
     const uint32_t pc = (gc - deg * t.cpd) * 4u;  // prime of the chunk's first word
-    const uint32_t r0 = bk.nrows * g / bk.G, r1 = bk.nrows * (g + 1) / bk.G;
+    uint32_t r0, r1;
+    tma_group_rows(bk, g, &r0, &r1);
+    const uint32_t gb = S.rp[r0], gn = S.rp[r1] - gb;
     const uint32_t col = ring_addr + c * 16u;  // chunk c of slot 0
     const uint32_t RB = t.cw * 16u;
     uint4 *out = reinterpret_cast<uint4 *>(t.out) + (size_t)bk.row0 * t.C + gc;
     const uint32_t gNS = g * bk.NS;
+    long long a0 = modred_bias(S.p[pc]), a1 = modred_bias(S.p[pc + 1]), a2 = modred_bias(S.p[pc + 2]),
+              a3 = modred_bias(S.p[pc + 3]);
+    uint32_t r = r0;
+    auto flush = [&]() {
+        if (active)
+            __stcs(out + (size_t)r * t.C, make_uint4(modred_reduce(a0, S.p[pc], S.m[pc], S.s[pc]),
+                                                     modred_reduce(a1, S.p[pc + 1], S.m[pc + 1], S.s[pc + 1]),
+                                                     modred_reduce(a2, S.p[pc + 2], S.m[pc + 2], S.s[pc + 2]),
+                                                     modred_reduce(a3, S.p[pc + 3], S.m[pc + 3], S.s[pc + 3])));
+        ++r;
+        a0 = modred_bias(S.p[pc]);
+        a1 = modred_bias(S.p[pc + 1]);
+        a2 = modred_bias(S.p[pc + 2]);
+        a3 = modred_bias(S.p[pc + 3]);
+    };
+    // rows end where the next row's edges start; empty rows end at once
+    while (r < r1 && S.rp[r + 1] == S.rp[r]) flush();
+    uint32_t rend = r < r1 ? S.rp[r + 1] - gb : 0xffffffffu;  // group edge index one past row r's last
     uint32_t s = 0, ph = 0;
-    for (uint32_t r = r0; r < r1; ++r) {
-        const uint32_t ne = S.rp[r + 1] - S.rp[r];
-        long long a0 = modred_bias(S.p[pc]), a1 = modred_bias(S.p[pc + 1]), a2 = modred_bias(S.p[pc + 2]),
-                  a3 = modred_bias(S.p[pc + 3]);
-        for (uint32_t k = 0; k < ne; k += E) {
-            const uint32_t st = gNS + s;
-            if (!mbar_wait(smem_addr(&S.full_bar[st]), ph, S.deadline)) {
-                atomicOr(err, 1);
-                return;
-            }
-            int cf[E];
-            uint4 x[E];
+    for (uint32_t base = 0; base < gn; base += E) {
+        const uint32_t st = gNS + s;
+        if (!mbar_wait(smem_addr(&S.full_bar[st]), ph, S.deadline)) {
+            atomicOr(err, 1);
+            return;
+        }
+        int f[E];
+        uint4 x[E];
 #pragma unroll
-            for (int j = 0; j < E; ++j) {
-                const uint32_t slot = st * E + j;
-                cf[j] = S.cf[slot];
-                bool ld = active;
-                if (PRED) ld = ld && deg >= S.sh[slot];
-                x[j] = ld ? lds128(col + slot * RB) : make_uint4(0, 0, 0, 0);
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_addr(&S.empty_bar[st]));
+        for (int j = 0; j < E; ++j) {
+            const uint32_t slot = st * E + j;
+            f[j] = S.cf[slot];
+            bool ld = active;
+            if (PRED) ld = ld && deg >= S.sh[slot];
+            x[j] = ld ? lds128(col + slot * RB) : make_uint4(0, 0, 0, 0);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_addr(&S.empty_bar[st]));
 #pragma unroll
-            for (int j = 0; j < E; ++j) {
-                const long long f = cf[j];
-                a0 += (long long)(int)x[j].x * f;
-                a1 += (long long)(int)x[j].y * f;
-                a2 += (long long)(int)x[j].z * f;
-                a3 += (long long)(int)x[j].w * f;
-            }
-            if (++s == bk.NS) {
-                s = 0;
-                ph ^= 1u;
+        for (int j = 0; j < E; ++j) {
+            const long long k = f[j];
+            a0 += (long long)(int)x[j].x * k;
+            a1 += (long long)(int)x[j].y * k;
+            a2 += (long long)(int)x[j].z * k;
+            a3 += (long long)(int)x[j].w * k;
+            if (base + j + 1 == rend) {  // the last edge of row r (empty slots past gn never match)
+                flush();
+                while (r < r1 && S.rp[r + 1] == S.rp[r]) flush();
+                rend = r < r1 ? S.rp[r + 1] - gb : 0xffffffffu;
             }
         }
-        if (active)
-            __stcs(out + (size_t)r * t.C,
-                   make_uint4(modred_reduce(a0, S.p[pc], S.m[pc], S.s[pc]),
-                              modred_reduce(a1, S.p[pc + 1], S.m[pc + 1], S.s[pc + 1]),
-                              modred_reduce(a2, S.p[pc + 2], S.m[pc + 2], S.s[pc + 2]),
-                              modred_reduce(a3, S.p[pc + 3], S.m[pc + 3], S.s[pc + 3])));
+        if (++s == bk.NS) {
+            s = 0;
+            ph ^= 1u;
+        }
     }
 }
 
 template <int E>
-__global__ void __launch_bounds__(kTmaThreads, E == 4 ? 4 : 5)
+__global__ void __launch_bounds__(kTmaThreads, E >= 8 ? 3 : 4)
     gather_tma_kernel(const GatherTask *__restrict__ tasks, int n_tasks, uint32_t rpb, uint32_t ring_bytes, int *err) {
     extern __shared__ __align__(128) uint8_t ring[];
     __shared__ TmaShared S;
@@ -282,7 +286,9 @@ __global__ void __launch_bounds__(kTmaThreads, E == 4 ? 4 : 5)
         int mid = (lo + hi + 1) >> 1;
         if (tasks[mid].block_begin <= b) lo = mid; else hi = mid - 1;
     }
-    const GatherTask t = tasks[lo];
+    if (threadIdx.x == 0) S.task = tasks[lo];
+    __syncthreads();
+    const GatherTask &t = S.task;
     TmaBlock bk;
     bk.row0 = (b - t.block_begin) * rpb;
     bk.nrows = min(rpb, t.rows - bk.row0);
@@ -292,7 +298,7 @@ __global__ void __launch_bounds__(kTmaThreads, E == 4 ? 4 : 5)
     const uint32_t slots_g = min((uint32_t)kTmaMaxSlots / bk.G, ring_bytes / (bk.G * RB));
     bk.NS = slots_g / E;        // stages per group
     bk.act = (t.cw + 31) / 32;  // consumer warps with chunks, per group (<= 8 / G)
-    if (bk.NS == 0 || t.cw > 256 || t.cw == 0 || rpb > (uint32_t)kTmaMaxRows) {  // block-uniform refusal
+    if (bk.NS == 0 || bk.G * E > 32 || t.cw > 256 || t.cw == 0 || rpb > (uint32_t)kTmaMaxRows) {  // refusal
         if (threadIdx.x == 0) atomicOr(err, 8);
         return;
     }
@@ -315,7 +321,6 @@ __global__ void __launch_bounds__(kTmaThreads, E == 4 ? 4 : 5)
     const uint32_t warp = threadIdx.x >> 5;
     if (warp == 0) {
         tma_produce<E>(t, bk, S, ring, err);
-        tma_drain<E>(bk, S, err);
         return;
     }
     const uint32_t cwi = warp - 1, wpg = kTmaConsumers / bk.G;
@@ -365,12 +370,12 @@ int prepare_gather_tma() {
     if (dev < 0 || dev >= 64) return fail(CP_EINVAL, "device index");
     if (done[dev]) return CP_OK;
     int rc;
-    if ((rc = set_attr<1>()) || (rc = set_attr<2>()) || (rc = set_attr<4>())) return rc;
+    if ((rc = set_attr<1>()) || (rc = set_attr<2>()) || (rc = set_attr<4>()) || (rc = set_attr<8>())) return rc;
     done[dev] = true;
     return CP_OK;
 }
 
-// rpb: destination rows per block (16..128); edges: edges per stage (1, 2 or 4);
+// rpb: destination rows per block (16..128); edges: edges per stage (1, 2, 4 or 8);
 // ring_kb: shared-memory ring per block.
 int launch_gather_tma(const GatherTask *tasks_dev, int n_tasks, uint32_t total_blocks, int rpb, int *err,
                       cudaStream_t st, int edges, int ring_kb) {
@@ -384,7 +389,8 @@ int launch_gather_tma(const GatherTask *tasks_dev, int n_tasks, uint32_t total_b
         case 1: gather_tma_kernel<1><<<total_blocks, kTmaThreads, dyn, st>>>(tasks_dev, n_tasks, rpb, dyn, err); break;
         case 2: gather_tma_kernel<2><<<total_blocks, kTmaThreads, dyn, st>>>(tasks_dev, n_tasks, rpb, dyn, err); break;
         case 4: gather_tma_kernel<4><<<total_blocks, kTmaThreads, dyn, st>>>(tasks_dev, n_tasks, rpb, dyn, err); break;
-        default: return fail(CP_EINVAL, "TMA gather edges per stage must be 1, 2 or 4");
+        case 8: gather_tma_kernel<8><<<total_blocks, kTmaThreads, dyn, st>>>(tasks_dev, n_tasks, rpb, dyn, err); break;
+        default: return fail(CP_EINVAL, "TMA gather edges per stage must be 1, 2, 4 or 8");
     }
     CP_CUDA_TRY(cudaGetLastError());
     return CP_OK;
