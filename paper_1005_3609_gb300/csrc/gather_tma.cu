@@ -86,10 +86,12 @@ __device__ __forceinline__ uint32_t fast_div_u(uint32_t x, uint32_t magic) { ret
 // Shared state of one block.
 struct TmaShared {
     uint64_t full_bar[kTmaMaxSlots], empty_bar[kTmaMaxSlots];  // per stage (at most one stage per slot)
-    int cf[kTmaMaxSlots];          // per slot: the edge's coefficient
-    uint32_t sh[kTmaMaxSlots];     // per slot: the edge's shift (degrees)
-    uint32_t rp[kTmaMaxRows + 1];  // the block's row pointers
-    uint32_t p[CP_MAX_PRIMES], m[CP_MAX_PRIMES], s[CP_MAX_PRIMES];  // reduction constants per prime
+    alignas(16) int cf[kTmaMaxSlots];       // per slot: the edge's coefficient
+    alignas(16) uint32_t sh[kTmaMaxSlots];  // per slot: the edge's shift (degrees)
+    alignas(16) uint32_t p[CP_MAX_PRIMES];  // reduction constants per prime
+    alignas(16) uint32_t m[CP_MAX_PRIMES];
+    alignas(16) uint32_t s[CP_MAX_PRIMES];
+    uint32_t rp[kTmaMaxRows + 1];           // the block's row pointers
     long long deadline;            // clock64 limit of every wait
     GatherTask task;               // the block's task (read where needed, not held in registers)
     int abort_flag;
@@ -187,48 +189,87 @@ __device__ __forceinline__ void tma_produce(const GatherTask &t, const TmaBlock 
     }
 }
 
+// 16-byte shared load, executed only where pred != 0 (zero elsewhere), with
+// the predicate inside the instruction so that the warp does not branch.
+__device__ __forceinline__ uint4 lds128_if(uint32_t addr, uint32_t pred) {
+    uint4 v = make_uint4(0, 0, 0, 0);
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %5, 0;\n\t"
+        "@p ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n\t}"
+        : "+r"(v.x), "+r"(v.y), "+r"(v.z), "+r"(v.w)
+        : "r"(addr), "r"(pred));
+    return v;
+}
 __device__ __forceinline__ uint4 lds128(uint32_t addr) {
     uint4 v;
     asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
     return v;
 }
+// acc += a * b with a, b signed 32-bit (one widening multiply-add).
+__device__ __forceinline__ void mad_wide(long long &acc, uint32_t a, int b) {
+    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+}
+// Arrive on an mbarrier from the lanes where pred != 0, without branching.
+__device__ __forceinline__ void mbar_arrive_if(uint32_t a, uint32_t pred) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "@p mbarrier.arrive.shared::cta.b64 _, [%0];\n\t}" ::"r"(a), "r"(pred)
+        : "memory");
+}
+// Streaming 16-byte global store where pred != 0.
+__device__ __forceinline__ void stcs128_if(uint4 *ptr, uint4 v, uint32_t pred) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %5, 0;\n\t"
+        "@p st.global.cs.v4.u32 [%0], {%1, %2, %3, %4};\n\t}" ::"l"(ptr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w),
+        "r"(pred)
+        : "memory");
+}
 
 // ---------------------------------------------------------------- consumers
-// Per stage: load the E chunks and coefficients into registers, release the
-// stage, then accumulate edge by edge; after the last edge of a row (and for
-// the empty rows that follow it) reduce the four words and store them.
+// Per stage: the E coefficients, then edge by edge the chunk and its
+// multiply-adds; after the last edge of a row (and for the empty rows that
+// follow it) reduce the four words and store them; then release the stage.
+// Threads past the row's last chunk load a valid chunk and store nothing.
 // PRED: the warp holds chunks of degree < kTmaMaxShift, where a shifted copy
 // leaves the slot's low chunks unwritten and the shift must be checked.
 template <int E, bool PRED>
 __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock &bk, TmaShared &S, uint32_t ring_addr,
                                             uint32_t g, uint32_t c, int *err) {
     const uint32_t lane = threadIdx.x & 31;
-    const bool active = c < t.cw;
-    const uint32_t gc = t.c0 + c;  // chunk within the row
+    const uint32_t active = c < t.cw ? 1u : 0u;
+    const uint32_t cl = min(c, t.cw - 1);  // the chunk this thread reads
+    const uint32_t gc = t.c0 + cl;          // chunk within the row
     const uint32_t deg = fast_div_u(gc, t.magic_cpd);
-    const uint32_t pc = (gc - deg * t.cpd) * 4u;  // prime of the chunk's first word
+    const uint32_t pc = (gc - deg * t.cpd) * 4u;  // prime of the chunk's first word (a multiple of 4)
     uint32_t r0, r1;
     tma_group_rows(bk, g, &r0, &r1);
     const uint32_t gb = S.rp[r0], gn = S.rp[r1] - gb;
-    const uint32_t col = ring_addr + c * 16u;  // chunk c of slot 0
+    const uint32_t col = ring_addr + cl * 16u;  // chunk cl of slot 0
     const uint32_t RB = t.cw * 16u;
     uint4 *out = reinterpret_cast<uint4 *>(t.out) + (size_t)bk.row0 * t.C + gc;
+    const uint32_t C = t.C;
     const uint32_t gNS = g * bk.NS;
-    long long a0 = modred_bias(S.p[pc]), a1 = modred_bias(S.p[pc + 1]), a2 = modred_bias(S.p[pc + 2]),
-              a3 = modred_bias(S.p[pc + 3]);
+    long long a0, a1, a2, a3;
+    auto reset = [&]() {
+        const uint4 p = *reinterpret_cast<const uint4 *>(S.p + pc);
+        a0 = modred_bias(p.x);
+        a1 = modred_bias(p.y);
+        a2 = modred_bias(p.z);
+        a3 = modred_bias(p.w);
+    };
     uint32_t r = r0;
     auto flush = [&]() {
-        if (active)
-            __stcs(out + (size_t)r * t.C, make_uint4(modred_reduce(a0, S.p[pc], S.m[pc], S.s[pc]),
-                                                     modred_reduce(a1, S.p[pc + 1], S.m[pc + 1], S.s[pc + 1]),
-                                                     modred_reduce(a2, S.p[pc + 2], S.m[pc + 2], S.s[pc + 2]),
-                                                     modred_reduce(a3, S.p[pc + 3], S.m[pc + 3], S.s[pc + 3])));
+        const uint4 p = *reinterpret_cast<const uint4 *>(S.p + pc);
+        const uint4 m = *reinterpret_cast<const uint4 *>(S.m + pc);
+        const uint4 sh = *reinterpret_cast<const uint4 *>(S.s + pc);
+        stcs128_if(out + (size_t)r * C,
+                   make_uint4(modred_reduce(a0, p.x, m.x, sh.x), modred_reduce(a1, p.y, m.y, sh.y),
+                              modred_reduce(a2, p.z, m.z, sh.z), modred_reduce(a3, p.w, m.w, sh.w)),
+                   active);
         ++r;
-        a0 = modred_bias(S.p[pc]);
-        a1 = modred_bias(S.p[pc + 1]);
-        a2 = modred_bias(S.p[pc + 2]);
-        a3 = modred_bias(S.p[pc + 3]);
+        reset();
     };
+    reset();
     // rows end where the next row's edges start; empty rows end at once
     while (r < r1 && S.rp[r + 1] == S.rp[r]) flush();
     uint32_t rend = r < r1 ? S.rp[r + 1] - gb : 0xffffffffu;  // group edge index one past row r's last
@@ -240,30 +281,37 @@ __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock 
             return;
         }
         int f[E];
-        uint4 x[E];
-#pragma unroll
-        for (int j = 0; j < E; ++j) {
-            const uint32_t slot = st * E + j;
-            f[j] = S.cf[slot];
-            bool ld = active;
-            if (PRED) ld = ld && deg >= S.sh[slot];
-            x[j] = ld ? lds128(col + slot * RB) : make_uint4(0, 0, 0, 0);
+        const uint32_t slot0 = st * E;
+        if (E == 8) {
+            const int4 c0 = *reinterpret_cast<const int4 *>(S.cf + slot0);
+            const int4 c1 = *reinterpret_cast<const int4 *>(S.cf + slot0 + 4);
+            f[0] = c0.x; f[1] = c0.y; f[2] = c0.z; f[3] = c0.w;
+            f[4 % E] = c1.x; f[5 % E] = c1.y; f[6 % E] = c1.z; f[7 % E] = c1.w;
+        } else if (E == 4) {
+            const int4 c0 = *reinterpret_cast<const int4 *>(S.cf + slot0);
+            f[0] = c0.x; f[1 % E] = c0.y; f[2 % E] = c0.z; f[3 % E] = c0.w;
+        } else if (E == 2) {
+            const int2 c0 = *reinterpret_cast<const int2 *>(S.cf + slot0);
+            f[0] = c0.x; f[1 % E] = c0.y;
+        } else {
+            f[0] = S.cf[slot0];
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_addr(&S.empty_bar[st]));
+        const uint32_t a = col + slot0 * RB;
 #pragma unroll
         for (int j = 0; j < E; ++j) {
-            const long long k = f[j];
-            a0 += (long long)(int)x[j].x * k;
-            a1 += (long long)(int)x[j].y * k;
-            a2 += (long long)(int)x[j].z * k;
-            a3 += (long long)(int)x[j].w * k;
+            const uint4 x = PRED ? lds128_if(a + j * RB, deg >= S.sh[slot0 + j] ? 1u : 0u) : lds128(a + j * RB);
+            mad_wide(a0, x.x, f[j]);
+            mad_wide(a1, x.y, f[j]);
+            mad_wide(a2, x.z, f[j]);
+            mad_wide(a3, x.w, f[j]);
             if (base + j + 1 == rend) {  // the last edge of row r (empty slots past gn never match)
                 flush();
                 while (r < r1 && S.rp[r + 1] == S.rp[r]) flush();
                 rend = r < r1 ? S.rp[r + 1] - gb : 0xffffffffu;
             }
         }
+        __syncwarp();
+        mbar_arrive_if(smem_addr(&S.empty_bar[st]), lane == 0 ? 1u : 0u);
         if (++s == bk.NS) {
             s = 0;
             ph ^= 1u;

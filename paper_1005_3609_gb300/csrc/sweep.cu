@@ -333,8 +333,8 @@ extern "C" int cp_sweep_create(int lattice, int k, const uint32_t *primes, int n
     // warm-up run) and keep the fastest (tile, grouping)
     std::vector<int> tiles = tile ? std::vector<int>{tile}
                                   : std::vector<int>{make_tile(32, 48, 4), make_tile(64, 48, 4),
-                                                     make_tile(16, 48, 4), make_tile(32, 64, 8),
-                                                     make_tile(32, 48, 0), make_tile(32, 40, 2), 4};
+                                                     make_tile(32, 64, 8), make_tile(64, 64, 8),
+                                                     make_tile(16, 48, 4), make_tile(32, 40, 2), 4};
     std::vector<int> grps;
     if (prime_groups) grps = {prime_groups};
     else
