@@ -189,11 +189,11 @@ def table_layout(cp, args):
 
 
 def tile_name(tile):
-    rows, ring, edges = tile & 0xFFF, (tile >> 12) & 0xFF, (tile >> 20) & 15
+    rows, ring, edges, cpt = tile & 0xFFF, (tile >> 12) & 0xFF, (tile >> 20) & 15, (tile >> 24) & 15
     if rows <= 8:
         return "register gather kernel, %d rows/warp" % rows
-    return "TMA gather kernel, %d rows/block, %d KB ring, %s edge(s) per stage" % (rows, ring or 32,
-                                                                                 edges or "auto")
+    return "TMA gather kernel, %d rows/block, %s KB ring, %s edge(s) per stage, %s chunk(s) per thread" % (
+        rows, ring or "auto", edges or "auto", cpt or "auto")
 
 
 def plain_run(cp, torch, lattice, k, primes, stream):
@@ -686,7 +686,7 @@ def paper_arm(args):
     lattice, k = args.lattice, 41
     primes = cp.select_primes(synthetic_inputs.prime_draws(0, 128), 16)
     stream = torch.cuda.Stream()
-    tile = args.tile or (64 | (32 << 12))
+    tile = args.tile or 32  # TMA kernel, rows/block 32, ring, stages and chunks per thread picked by row width
     table_layout(cp, args)
     peak = (load_peaks() or {}).get("hbm_gbs") or 6800.0
     groups, res_all = [], []

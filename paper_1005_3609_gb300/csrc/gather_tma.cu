@@ -36,8 +36,7 @@
 
 namespace cp {
 
-constexpr int kTmaConsumers = 8;                      // consumer warps
-constexpr int kTmaThreads = 32 * (kTmaConsumers + 1);  // + producer warp
+constexpr int kTmaConsumers = 8;                      // consumer warps at one chunk per thread
 constexpr int kTmaMaxSlots = 96;                       // row slots per block (all groups)
 constexpr int kTmaMaxRows = 128;                       // destination rows per block
 constexpr int kTmaMaxShift = 3;                        // shifts of the edge format: 2 bits
@@ -226,46 +225,62 @@ __device__ __forceinline__ void stcs128_if(uint4 *ptr, uint4 v, uint32_t pred) {
 }
 
 // ---------------------------------------------------------------- consumers
-// Per stage: the E coefficients, then edge by edge the chunk and its
-// multiply-adds; after the last edge of a row (and for the empty rows that
-// follow it) reduce the four words and store them; then release the stage.
-// Threads past the row's last chunk load a valid chunk and store nothing.
-// PRED: the warp holds chunks of degree < kTmaMaxShift, where a shifted copy
-// leaves the slot's low chunks unwritten and the shift must be checked.
-template <int E, bool PRED>
+// A consumer thread owns CPT chunks of the row, c + k * stride (stride = the
+// chunks its group's warps cover side by side), so a warp's 16-byte loads
+// stay contiguous.  Per stage: the E coefficients, then edge by edge the
+// thread's chunks and their multiply-adds; after the last edge of a row (and
+// for the empty rows that follow it) reduce the words and store them; then
+// release the stage.  Chunks past the row's end are read from a valid chunk
+// and not stored.  PRED: the warp holds chunks of degree < kTmaMaxShift (only
+// the first chunk can), where a shifted copy leaves the slot's low chunks
+// unwritten and the shift must be checked.
+template <int E, int CPT, bool PRED>
 __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock &bk, TmaShared &S, uint32_t ring_addr,
-                                            uint32_t g, uint32_t c, int *err) {
+                                            uint32_t g, uint32_t c, uint32_t stride, int *err) {
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t active = c < t.cw ? 1u : 0u;
-    const uint32_t cl = min(c, t.cw - 1);  // the chunk this thread reads
-    const uint32_t gc = t.c0 + cl;          // chunk within the row
-    const uint32_t deg = fast_div_u(gc, t.magic_cpd);
-    const uint32_t pc = (gc - deg * t.cpd) * 4u;  // prime of the chunk's first word (a multiple of 4)
+    uint32_t col[CPT], gcs[CPT], pcs[CPT], active[CPT];
+    uint32_t deg0 = 0;
+#pragma unroll
+    for (int k = 0; k < CPT; ++k) {
+        const uint32_t ck = c + k * stride;
+        active[k] = ck < t.cw ? 1u : 0u;
+        const uint32_t cl = min(ck, t.cw - 1);  // the chunk this thread reads
+        gcs[k] = t.c0 + cl;                      // chunk within the row
+        const uint32_t deg = fast_div_u(gcs[k], t.magic_cpd);
+        if (k == 0) deg0 = deg;
+        pcs[k] = (gcs[k] - deg * t.cpd) * 4u;  // prime of the chunk's first word (a multiple of 4)
+        col[k] = ring_addr + cl * 16u;
+    }
     uint32_t r0, r1;
     tma_group_rows(bk, g, &r0, &r1);
     const uint32_t gb = S.rp[r0], gn = S.rp[r1] - gb;
-    const uint32_t col = ring_addr + cl * 16u;  // chunk cl of slot 0
     const uint32_t RB = t.cw * 16u;
-    uint4 *out = reinterpret_cast<uint4 *>(t.out) + (size_t)bk.row0 * t.C + gc;
+    uint4 *out = reinterpret_cast<uint4 *>(t.out) + (size_t)bk.row0 * t.C;
     const uint32_t C = t.C;
     const uint32_t gNS = g * bk.NS;
-    long long a0, a1, a2, a3;
+    long long a[CPT][4];
     auto reset = [&]() {
-        const uint4 p = *reinterpret_cast<const uint4 *>(S.p + pc);
-        a0 = modred_bias(p.x);
-        a1 = modred_bias(p.y);
-        a2 = modred_bias(p.z);
-        a3 = modred_bias(p.w);
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            const uint4 p = *reinterpret_cast<const uint4 *>(S.p + pcs[k]);
+            a[k][0] = modred_bias(p.x);
+            a[k][1] = modred_bias(p.y);
+            a[k][2] = modred_bias(p.z);
+            a[k][3] = modred_bias(p.w);
+        }
     };
     uint32_t r = r0;
     auto flush = [&]() {
-        const uint4 p = *reinterpret_cast<const uint4 *>(S.p + pc);
-        const uint4 m = *reinterpret_cast<const uint4 *>(S.m + pc);
-        const uint4 sh = *reinterpret_cast<const uint4 *>(S.s + pc);
-        stcs128_if(out + (size_t)r * C,
-                   make_uint4(modred_reduce(a0, p.x, m.x, sh.x), modred_reduce(a1, p.y, m.y, sh.y),
-                              modred_reduce(a2, p.z, m.z, sh.z), modred_reduce(a3, p.w, m.w, sh.w)),
-                   active);
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            const uint4 p = *reinterpret_cast<const uint4 *>(S.p + pcs[k]);
+            const uint4 m = *reinterpret_cast<const uint4 *>(S.m + pcs[k]);
+            const uint4 sh = *reinterpret_cast<const uint4 *>(S.s + pcs[k]);
+            stcs128_if(out + (size_t)r * C + gcs[k],
+                       make_uint4(modred_reduce(a[k][0], p.x, m.x, sh.x), modred_reduce(a[k][1], p.y, m.y, sh.y),
+                                  modred_reduce(a[k][2], p.z, m.z, sh.z), modred_reduce(a[k][3], p.w, m.w, sh.w)),
+                       active[k]);
+        }
         ++r;
         reset();
     };
@@ -285,7 +300,7 @@ __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock 
         if (E == 8) {
             const int4 c0 = *reinterpret_cast<const int4 *>(S.cf + slot0);
             const int4 c1 = *reinterpret_cast<const int4 *>(S.cf + slot0 + 4);
-            f[0] = c0.x; f[1] = c0.y; f[2] = c0.z; f[3] = c0.w;
+            f[0] = c0.x; f[1 % E] = c0.y; f[2 % E] = c0.z; f[3 % E] = c0.w;
             f[4 % E] = c1.x; f[5 % E] = c1.y; f[6 % E] = c1.z; f[7 % E] = c1.w;
         } else if (E == 4) {
             const int4 c0 = *reinterpret_cast<const int4 *>(S.cf + slot0);
@@ -296,14 +311,18 @@ __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock 
         } else {
             f[0] = S.cf[slot0];
         }
-        const uint32_t a = col + slot0 * RB;
+        const uint32_t so = slot0 * RB;
 #pragma unroll
         for (int j = 0; j < E; ++j) {
-            const uint4 x = PRED ? lds128_if(a + j * RB, deg >= S.sh[slot0 + j] ? 1u : 0u) : lds128(a + j * RB);
-            mad_wide(a0, x.x, f[j]);
-            mad_wide(a1, x.y, f[j]);
-            mad_wide(a2, x.z, f[j]);
-            mad_wide(a3, x.w, f[j]);
+#pragma unroll
+            for (int k = 0; k < CPT; ++k) {
+                const uint32_t addr = col[k] + so + j * RB;
+                const uint4 x = (PRED && k == 0) ? lds128_if(addr, deg0 >= S.sh[slot0 + j] ? 1u : 0u) : lds128(addr);
+                mad_wide(a[k][0], x.x, f[j]);
+                mad_wide(a[k][1], x.y, f[j]);
+                mad_wide(a[k][2], x.z, f[j]);
+                mad_wide(a[k][3], x.w, f[j]);
+            }
             if (base + j + 1 == rend) {  // the last edge of row r (empty slots past gn never match)
                 flush();
                 while (r < r1 && S.rp[r + 1] == S.rp[r]) flush();
@@ -319,11 +338,14 @@ __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock 
     }
 }
 
-template <int E>
-__global__ void __launch_bounds__(kTmaThreads, E >= 8 ? 3 : 4)
+__host__ __device__ constexpr int tma_threads(int CPT) { return 32 * (1 + kTmaConsumers / CPT); }
+
+template <int E, int CPT>
+__global__ void __launch_bounds__(tma_threads(CPT), tma_min_blocks(E, CPT))
     gather_tma_kernel(const GatherTask *__restrict__ tasks, int n_tasks, uint32_t rpb, uint32_t ring_bytes, int *err) {
     extern __shared__ __align__(128) uint8_t ring[];
     __shared__ TmaShared S;
+    constexpr uint32_t W = kTmaConsumers / CPT;  // consumer warps
 
     if (threadIdx.x == 0) S.abort_flag = *(volatile int *)err;  // a previous block gave up: do nothing
     __syncthreads();
@@ -341,11 +363,12 @@ __global__ void __launch_bounds__(kTmaThreads, E >= 8 ? 3 : 4)
     bk.row0 = (b - t.block_begin) * rpb;
     bk.nrows = min(rpb, t.rows - bk.row0);
     const uint32_t RB = t.cw * 16u;
-    bk.G = 1;
-    while (bk.G < 8 && 2 * bk.G * t.cw <= 256) bk.G *= 2;
+    bk.G = 1;  // row groups: each group's warps cover 256 / G chunks
+    while (bk.G < W && 2 * bk.G * t.cw <= 256) bk.G *= 2;
     const uint32_t slots_g = min((uint32_t)kTmaMaxSlots / bk.G, ring_bytes / (bk.G * RB));
-    bk.NS = slots_g / E;        // stages per group
-    bk.act = (t.cw + 31) / 32;  // consumer warps with chunks, per group (<= 8 / G)
+    bk.NS = slots_g / E;                                 // stages per group
+    const uint32_t wpg = W / bk.G;                       // consumer warps per group
+    bk.act = min(wpg, (t.cw + 31) / 32);                 // warps with chunks, per group
     if (bk.NS == 0 || bk.G * E > 32 || t.cw > 256 || t.cw == 0 || rpb > (uint32_t)kTmaMaxRows) {  // refusal
         if (threadIdx.x == 0) atomicOr(err, 8);
         return;
@@ -371,15 +394,16 @@ __global__ void __launch_bounds__(kTmaThreads, E >= 8 ? 3 : 4)
         tma_produce<E>(t, bk, S, ring, err);
         return;
     }
-    const uint32_t cwi = warp - 1, wpg = kTmaConsumers / bk.G;
+    const uint32_t cwi = warp - 1;
     const uint32_t g = cwi / wpg, wi = cwi - g * wpg;
     if (wi >= bk.act) return;  // all of this warp's chunks lie beyond the row
     const uint32_t c = wi * 32 + (threadIdx.x & 31);
+    const uint32_t stride = 32 * wpg;  // chunks the group's warps cover side by side
     const uint32_t ring_addr = smem_addr(ring);
     if (t.c0 + wi * 32 < (uint32_t)kTmaMaxShift * t.cpd)
-        tma_consume<E, true>(t, bk, S, ring_addr, g, c, err);
+        tma_consume<E, CPT, true>(t, bk, S, ring_addr, g, c, stride, err);
     else
-        tma_consume<E, false>(t, bk, S, ring_addr, g, c, err);
+        tma_consume<E, CPT, false>(t, bk, S, ring_addr, g, c, stride, err);
 }
 
 // Ring sizes: ring_kb KB per block (several blocks per SM).
@@ -388,10 +412,19 @@ constexpr uint32_t kTmaRingMin = 16 * 1024;
 
 bool tma_usable(const GatherTask &t) { return t.vec4 && t.cw >= 1 && t.cw <= 256; }
 
-template <int E>
+template <int E, int CPT>
 static int set_attr() {
-    CP_CUDA_TRY(cudaFuncSetAttribute(gather_tma_kernel<E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CP_CUDA_TRY(cudaFuncSetAttribute(gather_tma_kernel<E, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kTmaRingMax));
+    return CP_OK;
+}
+
+template <int CPT>
+static int set_attrs() {
+    int rc;
+    if ((rc = set_attr<1, CPT>()) || (rc = set_attr<2, CPT>()) || (rc = set_attr<4, CPT>()) ||
+        (rc = set_attr<8, CPT>()))
+        return rc;
     return CP_OK;
 }
 
@@ -418,28 +451,43 @@ int prepare_gather_tma() {
     if (dev < 0 || dev >= 64) return fail(CP_EINVAL, "device index");
     if (done[dev]) return CP_OK;
     int rc;
-    if ((rc = set_attr<1>()) || (rc = set_attr<2>()) || (rc = set_attr<4>()) || (rc = set_attr<8>())) return rc;
+    if ((rc = set_attrs<1>()) || (rc = set_attrs<2>()) || (rc = set_attrs<4>())) return rc;
     done[dev] = true;
     return CP_OK;
 }
 
+template <int CPT>
+static int launch_cpt(const GatherTask *tasks_dev, int n_tasks, uint32_t blocks, uint32_t rpb, uint32_t dyn, int *err,
+                      cudaStream_t st, int edges) {
+    constexpr int T = tma_threads(CPT);
+    switch (edges) {
+        case 1: gather_tma_kernel<1, CPT><<<blocks, T, dyn, st>>>(tasks_dev, n_tasks, rpb, dyn, err); break;
+        case 2: gather_tma_kernel<2, CPT><<<blocks, T, dyn, st>>>(tasks_dev, n_tasks, rpb, dyn, err); break;
+        case 4: gather_tma_kernel<4, CPT><<<blocks, T, dyn, st>>>(tasks_dev, n_tasks, rpb, dyn, err); break;
+        case 8: gather_tma_kernel<8, CPT><<<blocks, T, dyn, st>>>(tasks_dev, n_tasks, rpb, dyn, err); break;
+        default: return fail(CP_EINVAL, "TMA gather edges per stage must be 1, 2, 4 or 8");
+    }
+    return CP_OK;
+}
+
 // rpb: destination rows per block (16..128); edges: edges per stage (1, 2, 4 or 8);
-// ring_kb: shared-memory ring per block.
+// cpt: 16-byte chunks per consumer thread (1, 2 or 4); ring_kb: shared-memory ring per block.
 int launch_gather_tma(const GatherTask *tasks_dev, int n_tasks, uint32_t total_blocks, int rpb, int *err,
-                      cudaStream_t st, int edges, int ring_kb) {
+                      cudaStream_t st, int edges, int ring_kb, int cpt) {
     if (n_tasks <= 0 || total_blocks == 0) return CP_OK;
     if (rpb != 16 && rpb != 32 && rpb != 64 && rpb != 128)
         return fail(CP_EINVAL, "TMA gather rows per block must be 16, 32, 64 or 128");
     uint32_t dyn = (uint32_t)ring_kb * 1024u;
     if (dyn < kTmaRingMin) dyn = kTmaRingMin;
     if (dyn > kTmaRingMax) dyn = kTmaRingMax;
-    switch (edges) {
-        case 1: gather_tma_kernel<1><<<total_blocks, kTmaThreads, dyn, st>>>(tasks_dev, n_tasks, rpb, dyn, err); break;
-        case 2: gather_tma_kernel<2><<<total_blocks, kTmaThreads, dyn, st>>>(tasks_dev, n_tasks, rpb, dyn, err); break;
-        case 4: gather_tma_kernel<4><<<total_blocks, kTmaThreads, dyn, st>>>(tasks_dev, n_tasks, rpb, dyn, err); break;
-        case 8: gather_tma_kernel<8><<<total_blocks, kTmaThreads, dyn, st>>>(tasks_dev, n_tasks, rpb, dyn, err); break;
-        default: return fail(CP_EINVAL, "TMA gather edges per stage must be 1, 2, 4 or 8");
+    int rc;
+    switch (cpt) {
+        case 1: rc = launch_cpt<1>(tasks_dev, n_tasks, total_blocks, rpb, dyn, err, st, edges); break;
+        case 2: rc = launch_cpt<2>(tasks_dev, n_tasks, total_blocks, rpb, dyn, err, st, edges); break;
+        case 4: rc = launch_cpt<4>(tasks_dev, n_tasks, total_blocks, rpb, dyn, err, st, edges); break;
+        default: return fail(CP_EINVAL, "TMA gather chunks per thread must be 1, 2 or 4");
     }
+    if (rc) return rc;
     CP_CUDA_TRY(cudaGetLastError());
     return CP_OK;
 }

@@ -169,7 +169,7 @@ static int make_strip(std::shared_ptr<TableSet> tabs, int lattice, int L, const 
     {
         std::vector<GatherTask> probe;
         append_gather_tasks(&probe, ts.row[0], s->vec[0], s->vec[1], s->primes_dev, s->D1, s->P);
-        s->tile = effective_tile(probe, 64);
+        s->tile = effective_tile(probe, make_tile(32, 0, 0, 0));
     }
     // launches of one row (starting from vec[b]) and of the read-out chain from vec[b]
     std::vector<GatherTask> all;

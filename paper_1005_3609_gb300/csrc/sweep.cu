@@ -305,14 +305,17 @@ extern "C" int cp_sweep_create(int lattice, int k, const uint32_t *primes, int n
     if (rc) return rc;
     if (!cuda_stream) return fail(CP_EINVAL, "the sweep needs a non-default stream (graph capture)");
     {
-        const int rows = tile & 0xFFF, ring = (tile >> 12) & 0xFF, edges = (tile >> 20) & 15;
+        const int rows = tile & 0xFFF, ring = (tile >> 12) & 0xFF, edges = (tile >> 20) & 15,
+                  cpt = (tile >> 24) & 15;
         const bool reg = (rows == 1 || rows == 2 || rows == 4 || rows == 8) && (tile >> 12) == 0;
-        const bool tma = (rows == 16 || rows == 32 || rows == 64 || rows == 128) && (tile >> 24) == 0 &&
+        const bool tma = (rows == 16 || rows == 32 || rows == 64 || rows == 128) && (tile >> 28) == 0 &&
+                         (cpt <= 2 || cpt == 4) &&
                          (ring == 0 || (ring >= 16 && ring <= 192)) &&
                          (edges <= 2 || edges == 4 || edges == 8);
         if (tile != 0 && !reg && !tma)
             return fail(CP_EINVAL, "tile must be 0 (autotune), 1, 2, 4, 8 (register kernel) or 16, 32, 64, 128 "
-                                   "(TMA) + (ring KB 16..192 << 12) + (edges per stage 1, 2, 4, 8 << 20)");
+                                   "(TMA) + (ring KB 16..192 << 12) + (edges per stage 1, 2, 4, 8 << 20) + "
+                                   "(chunks per thread 1, 2, 4 << 24)");
     }
     if (prime_groups < 0 || (prime_groups > 0 && n_primes % prime_groups != 0))
         return fail(CP_EINVAL, "prime_groups must divide n_primes");
@@ -332,9 +335,10 @@ extern "C" int cp_sweep_create(int lattice, int k, const uint32_t *primes, int n
     // launch program for each candidate tile, time one graph run (after a
     // warm-up run) and keep the fastest (tile, grouping)
     std::vector<int> tiles = tile ? std::vector<int>{tile}
-                                  : std::vector<int>{make_tile(32, 48, 4), make_tile(64, 48, 4),
-                                                     make_tile(32, 64, 8), make_tile(64, 64, 8),
-                                                     make_tile(16, 48, 4), make_tile(32, 40, 2), 4};
+                                  : std::vector<int>{make_tile(32, 0, 0, 0), make_tile(64, 0, 0, 0),
+                                                     make_tile(32, 48, 4, 2), make_tile(64, 48, 4, 2),
+                                                     make_tile(32, 64, 8, 1), make_tile(64, 64, 8, 1),
+                                                     make_tile(16, 0, 0, 0), 4};
     std::vector<int> grps;
     if (prime_groups) grps = {prime_groups};
     else

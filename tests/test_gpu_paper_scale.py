@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 cp = pytest.importorskip("paper_1005_3609_gb300")
 
-TILE = 64 | (28 << 12) | (1 << 20)  # TMA gather, 64 rows per block, 28 KB ring (no autotune at this size)
+TILE = 32  # TMA gather, 32 rows per block, stages and chunks per thread picked from the row width (no autotune at this size)
 
 
 @pytest.fixture(scope="module")

@@ -65,7 +65,9 @@ def test_tile_and_group_choices_agree(stream, k):
     # TMA kernel runs 2, 4 and 8 consumer row groups
     primes = gpu_util.seed_primes(16, seed=2)
     ref = None
-    for tile in (1, 2, 4, 8, 16, 32, 64, 128):
+    # register kernel, TMA kernel with default stages, and every edges-per-stage x chunks-per-thread variant
+    tma = [32 | (48 << 12) | (e << 20) | (c << 24) for e in (1, 2, 4, 8) for c in (1, 2, 4)]
+    for tile in [1, 2, 4, 8, 16, 32, 64, 128] + tma:
         for groups in (1, 2, 4):
             with cp.Sweep("square", k, primes, stream, tile=tile, prime_groups=groups) as sw:
                 sw.run()
