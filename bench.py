@@ -179,10 +179,14 @@ def gather_source_sha():
 
 
 def table_layout(cp, args):
-    """Apply --per-site-tables and describe the layout of the transfer-matrix tables."""
-    cp.set_factor_pairing(0 if args.per_site_tables else 1)
-    if args.per_site_tables:
+    """Apply --per-site-tables / --pairing and describe the layout of the transfer-matrix tables."""
+    mode = 0 if args.per_site_tables else (args.pairing if args.pairing is not None else 1)
+    cp.set_factor_pairing(mode)
+    if mode == 0:
         return "one table per site factor (r launches per row)"
+    if mode == 3:
+        return ("two-site tables on both lattices: consecutive site factors composed in pairs (ceil(r/2) launches "
+                "per row, the intermediate vector never written); updates counted per site factor")
     return ("square lattice, rows >= 3 KB: two-site tables, consecutive site factors composed in pairs (ceil(r/2) "
             "launches per row, the intermediate vector never written); otherwise one table per site factor; "
             "updates counted per site factor either way")
@@ -775,18 +779,18 @@ def reference_arm(args):
 # ---------------------------------------------------------------- probe workload (one wide strip)
 
 def _probe_oracle_job(args):
-    L, rows, D, p = args
+    lattice, L, rows, D, p = args
     from oracle import modp
     t = time.perf_counter()
-    modp.ptilde_heights("square", L, [rows + 1], D, p)
+    modp.ptilde_heights(lattice, L, [rows + 1], D, p)
     return time.perf_counter() - t
 
 
 def probe_arm(args):
-    """One square strip of width L (default 18: 3 210 246 intermediate states,
-    12.9 GB per vector at D = 62 and 16 primes): each step resets it to e_0,
-    advances `rows` rows (L per-site launches each) and reads P~ out.  The
-    per-site kernel runs far beyond the L2 here."""
+    """One strip of width L (default: square, width 18, 3 210 246 intermediate
+    states, 12.9 GB per vector at D = 62 and 16 primes): each step resets it to
+    e_0, advances `rows` rows and reads P~ out.  The per-site kernel runs far
+    beyond the L2 here.  --lattice triangular gives the triangular strip."""
     import torch
     import paper_1005_3609_gb300 as cp
     pool = None
@@ -797,7 +801,8 @@ def probe_arm(args):
     stream = torch.cuda.Stream()
     t_setup = time.perf_counter()
     layout = table_layout(cp, args)
-    s = cp.Strip("square", L, primes, max_degree=D, max_rows=rows + 1, stream=stream)
+    lattice = args.lattice
+    s = cp.Strip(lattice, L, primes, max_degree=D, max_rows=rows + 1, stream=stream)
     setup_s = time.perf_counter() - t_setup
     row_upd, row_own, ro_upd, ro_own, row_bytes, ro_bytes = s.work()
     paired = row_own < row_bytes
@@ -838,7 +843,7 @@ def probe_arm(args):
     peak = (peaks or {}).get("hbm_gbs") or 6800.0
     achieved = row_bytes / (row_ms / 1e3) / 1e9  # per-update algorithmic bytes (one factor at a time)
     own = row_own / (row_ms / 1e3) / 1e9        # bytes the launched tables need
-    traffic = load_traffic("gather_kernel:probe:square:L%d:D%d:P%d:%s" % (L, D, P,
+    traffic = load_traffic("gather_kernel:probe:%s:L%d:D%d:P%d:%s" % (lattice, L, D, P,
                                                                           "site" if args.per_site_tables else "auto"))
     # e2e through the C ABI: the read-out copied to host memory every step
     host = None
@@ -853,8 +858,9 @@ def probe_arm(args):
     res = {"metric": "state-coeff updates/s (one wide strip, per-site gather)", "value": value, "unit": "updates/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-           "config": {"workload": "square strip width %d (%d NCNNN / %d intermediate states), %d primes, D=%d: "
-                                  "reset to e_0, %d rows, read-out" % (L, n_states[0], n_states[1], P, D, rows),
+           "config": {"workload": "%s strip width %d (%d NCNNN / %d intermediate states), %d primes, D=%d: "
+                                  "reset to e_0, %d rows, read-out" % (lattice, L, n_states[0], n_states[1], P, D,
+                                                                       rows),
                       "l2": "no flush: vectors %.1f GB each, > 100x L2" % (n_states[1] * (D + 1) * P * 4 / 1e9),
                       "tables": "built before timing (%.1f s)" % setup_s, "tile": "strip default (TMA gather)",
                       "factor_tables": layout,
@@ -875,14 +881,14 @@ def probe_arm(args):
     if pool is not None:
         cL, cP = args.probe_cpu_L, min(P, min(16, os.cpu_count() or 1))
         t = time.perf_counter()
-        pool.map(_probe_oracle_job, [(cL, rows, D, p) for p in primes[:cP]])
+        pool.map(_probe_oracle_job, [(lattice, cL, rows, D, p) for p in primes[:cP]])
         wall = time.perf_counter() - t
-        with cp.Strip("square", cL, primes[:1], max_degree=D, max_rows=rows + 1) as sc:
+        with cp.Strip(lattice, cL, primes[:1], max_degree=D, max_rows=rows + 1) as sc:
             ru, _, ou, _, _, _ = sc.work()
         cupd = (rows * ru + ou) * cP
         res["cpu_baseline"] = {"value": cupd / wall, "unit": "updates/s", "cores": cP, "kind": "oracle",
-                               "sample": "plain-C mod-p oracle (hash-map TM), square width %d, %d rows, D=%d, %d "
-                                         "primes (one process each), %.1f s wall" % (cL, rows, D, cP, wall)}
+                               "sample": "plain-C mod-p oracle (hash-map TM), %s width %d, %d rows, D=%d, %d "
+                                         "primes (one process each), %.1f s wall" % (lattice, cL, rows, D, cP, wall)}
         pool.close()
     print(json.dumps(res))
 
@@ -914,6 +920,8 @@ def main():
                     help="skip the further workloads of the default line (triangular sweep, configs 2/3, serving)")
     ap.add_argument("--serve-prefix", type=int, default=100,
                     help="requests of the serving stream run on the default line")
+    ap.add_argument("--pairing", type=int, default=None, choices=[0, 1, 2, 3],
+                    help="table layout (cp_set_factor_pairing): 1 default, 3 two-site tables on both lattices")
     ap.add_argument("--per-site-tables", action="store_true",
                     help="one table per site factor instead of two-site tables (same results)")
     args = ap.parse_args()

@@ -136,7 +136,7 @@ int cp_strip_reset(cp_strip *s);
 void cp_destroy(cp_strip *s);
 
 /*
- * cp_set_factor_pairing -- how the square-lattice chromatic tables built from
+ * cp_set_factor_pairing -- how the chromatic tables built from
  * now on are laid out (strips, sweeps and server jobs created afterwards;
  * tables already built stay cached under their own layout).  A two-site table
  * is the product of a consecutive pair of per-site factors, T_2 T_1, T_4 T_3,
@@ -145,10 +145,10 @@ void cp_destroy(cp_strip *s);
  * of each pair is never written -- the same matrix product as the
  * factorisation of Sec. 3.2 with half the vector traffic but as many edge
  * copies, which pays only when a state's row, (D+1) n_primes words, is a few
- * KB long.  mode 1 (the default): two-site tables for rows of at least 3 KB;
- * mode 2: for every square-lattice strip; mode 0: one table per factor, as in
- * the paper.  Triangular tables are always one per factor.  Results are
- * identical in every mode.  Returns the previous mode.  Not thread-safe
+ * KB long.  mode 1 (the default): two-site tables for square-lattice rows of
+ * at least 3 KB; mode 2: for every square-lattice strip; mode 3: for every
+ * strip of both lattices; mode 0: one table per factor, as in the paper.
+ * Results are identical in every mode.  Returns the previous mode.  Not thread-safe
  * against concurrent strip creation.
  */
 int cp_set_factor_pairing(int mode);

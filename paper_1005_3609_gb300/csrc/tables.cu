@@ -723,7 +723,7 @@ static int build_potts_tableset(int lattice, int L, int v, cudaStream_t st, std:
 
 static std::mutex g_cache_mu;
 static std::map<std::tuple<int, int, int>, std::shared_ptr<TableSet>> g_cache[64];  // per device
-static int g_pairing = 1;  // 0 never, 1 square rows of >= kPairRowBytes, 2 every square table
+static int g_pairing = 1;  // 0 never, 1 square rows of >= kPairRowBytes, 2 every square table, 3 every table
 
 int factor_pairing() {
     std::lock_guard<std::mutex> lk(g_cache_mu);
@@ -733,7 +733,7 @@ int factor_pairing() {
 int set_factor_pairing(int mode) {
     std::lock_guard<std::mutex> lk(g_cache_mu);
     const int old = g_pairing;
-    g_pairing = mode < 0 ? 0 : (mode > 2 ? 2 : mode);
+    g_pairing = mode < 0 ? 0 : (mode > 3 ? 3 : mode);
     return old;
 }
 static std::map<std::tuple<int, int, int>, std::shared_ptr<TableSet>> g_potts_cache[64];
@@ -747,7 +747,8 @@ int get_tables(int lattice, int L, size_t row_bytes, cudaStream_t st, std::share
     // which set the pace on narrow rows: they pay on square-lattice rows of a few
     // KB and more; on the triangular lattice a pair has up to 21 terms per source
     // and the gathers ran slower than one factor at a time.
-    const int paired = lattice == CP_SQUARE && (g_pairing == 2 || (g_pairing == 1 && row_bytes >= kPairRowBytes));
+    const int paired = g_pairing == 3 ||
+                       (lattice == CP_SQUARE && (g_pairing == 2 || (g_pairing == 1 && row_bytes >= kPairRowBytes)));
     auto key = std::make_tuple(lattice, L, paired);
     auto it = g_cache[dev].find(key);
     if (it != g_cache[dev].end()) {
@@ -784,7 +785,7 @@ int get_potts_tables(int lattice, int L, int v, cudaStream_t st, std::shared_ptr
 // Copy one cached (or freshly built) chromatic table to the host.
 int debug_table(int lattice, int L, int paired, int which, int index, uint32_t *row_ptr_host, uint64_t max_rows,
                 uint32_t *edges_host, uint64_t max_edges, uint64_t info[4]) {
-    const int old = set_factor_pairing(paired ? 2 : 0);
+    const int old = set_factor_pairing(paired ? 3 : 0);
     std::shared_ptr<TableSet> ts;
     int rc = get_tables(lattice, L, 0, 0, &ts);
     set_factor_pairing(old);

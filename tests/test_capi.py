@@ -81,11 +81,11 @@ def test_newer_entry_points_validate_without_gpu(lib):
     assert lib.cp_create_strip_potts(0, 4, 2, one, 1, -1, 0, None, ctypes.byref(h)) == -1  # max_rows
     assert lib.cp_strip_work(None, (ctypes.c_uint64 * 6)()) == -1
     assert lib.cp_sweep_work(None, (ctypes.c_uint64 * 3)()) == -1
-    # the pairing switch returns the previous mode and clamps to 0..2
+    # the pairing switch returns the previous mode and clamps to 0..3
     old = lib.cp_set_factor_pairing(0)
-    assert old in (0, 1, 2)
+    assert old in (0, 1, 2, 3)
     assert lib.cp_set_factor_pairing(7) == 0
-    assert lib.cp_set_factor_pairing(old) == 2
+    assert lib.cp_set_factor_pairing(old) == 3
 
 
 def test_whitney_bits_on_host(lib):
