@@ -251,6 +251,12 @@ __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock 
         pcs[k] = (gcs[k] - deg * t.cpd) * 4u;  // prime of the chunk's first word (a multiple of 4)
         col[k] = ring_addr + cl * 16u;
     }
+    // reduction constants of the first chunk's four primes, kept in registers; the other
+    // chunks have the same primes when the stride is a multiple of the chunks per degree
+    const bool same_primes = stride % t.cpd == 0;
+    const uint4 P0 = *reinterpret_cast<const uint4 *>(S.p + pcs[0]);
+    const uint4 M0 = *reinterpret_cast<const uint4 *>(S.m + pcs[0]);
+    const uint4 S0 = *reinterpret_cast<const uint4 *>(S.s + pcs[0]);
     uint32_t r0, r1;
     tma_group_rows(bk, g, &r0, &r1);
     const uint32_t gb = S.rp[r0], gn = S.rp[r1] - gb;
@@ -262,7 +268,7 @@ __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock 
     auto reset = [&]() {
 #pragma unroll
         for (int k = 0; k < CPT; ++k) {
-            const uint4 p = *reinterpret_cast<const uint4 *>(S.p + pcs[k]);
+            const uint4 p = (k == 0 || same_primes) ? P0 : *reinterpret_cast<const uint4 *>(S.p + pcs[k]);
             a[k][0] = modred_bias(p.x);
             a[k][1] = modred_bias(p.y);
             a[k][2] = modred_bias(p.z);
@@ -273,9 +279,12 @@ __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock 
     auto flush = [&]() {
 #pragma unroll
         for (int k = 0; k < CPT; ++k) {
-            const uint4 p = *reinterpret_cast<const uint4 *>(S.p + pcs[k]);
-            const uint4 m = *reinterpret_cast<const uint4 *>(S.m + pcs[k]);
-            const uint4 sh = *reinterpret_cast<const uint4 *>(S.s + pcs[k]);
+            uint4 p = P0, m = M0, sh = S0;
+            if (k > 0 && !same_primes) {
+                p = *reinterpret_cast<const uint4 *>(S.p + pcs[k]);
+                m = *reinterpret_cast<const uint4 *>(S.m + pcs[k]);
+                sh = *reinterpret_cast<const uint4 *>(S.s + pcs[k]);
+            }
             stcs128_if(out + (size_t)r * C + gcs[k],
                        make_uint4(modred_reduce(a[k][0], p.x, m.x, sh.x), modred_reduce(a[k][1], p.y, m.y, sh.y),
                                   modred_reduce(a[k][2], p.z, m.z, sh.z), modred_reduce(a[k][3], p.w, m.w, sh.w)),
