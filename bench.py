@@ -803,6 +803,8 @@ def probe_arm(args):
     layout = table_layout(cp, args)
     lattice = args.lattice
     s = cp.Strip(lattice, L, primes, max_degree=D, max_rows=rows + 1, stream=stream)
+    if args.tile:
+        s.set_tile(args.tile)
     setup_s = time.perf_counter() - t_setup
     row_upd, row_own, ro_upd, ro_own, row_bytes, ro_bytes = s.work()
     paired = row_own < row_bytes

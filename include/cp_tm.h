@@ -129,6 +129,12 @@ int cp_strip_info(const cp_strip *s, uint64_t n_states[2], int *degree, int *hei
  * at a time (intermediate vectors included).  No GPU work. */
 int cp_strip_work(const cp_strip *s, uint64_t work[6]);
 
+/* Gather tile of the strip's launches, encoded as cp_sweep_create's tile
+ * (0 = the default: TMA kernel, 32 rows per block, stages, chunks per thread
+ * and ring picked from the row width).  A tuning knob: results are identical
+ * for every tile.  Synchronises the strip's stream.  CP_EINVAL on a bad tile. */
+int cp_strip_set_tile(cp_strip *s, int tile);
+
 /* Restart the strip at height 1 with the state vector e_0 (keeps its tables
  * and buffers).  Asynchronous on the strip's stream. */
 int cp_strip_reset(cp_strip *s);

@@ -43,6 +43,7 @@ SIGNATURES = {
     "cp_strip_info": (ctypes.c_int, [vp, u64p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "cp_destroy": (None, [vp]),
     "cp_strip_reset": (ctypes.c_int, [vp]),
+    "cp_strip_set_tile": (ctypes.c_int, [vp, ctypes.c_int]),
     "cp_strip_work": (ctypes.c_int, [vp, u64p]),
     "cp_set_factor_pairing": (ctypes.c_int, [ctypes.c_int]),
     "cp_sweep_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, u32p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -258,6 +259,10 @@ class Strip:
 
     def reset(self):
         check("cp_strip_reset", load().cp_strip_reset(self._h))
+
+    def set_tile(self, tile):
+        """Gather tile of this strip's launches (cp_strip_set_tile; 0 = default)."""
+        check("cp_strip_set_tile", load().cp_strip_set_tile(self._h, int(tile)))
 
     def work(self):
         """(row updates, row bytes, read-out updates, read-out bytes, row bytes one factor at a

@@ -351,6 +351,27 @@ extern "C" int cp_strip_work(const cp_strip *s, uint64_t work[6]) {
     return CP_OK;
 }
 
+extern "C" int cp_strip_set_tile(cp_strip *s, int tile) {
+    if (!s) return fail(CP_EINVAL, "strip is NULL");
+    const int rows = tile & 0xFFF, ring = (tile >> 12) & 0xFF, edges = (tile >> 20) & 15, cpt = (tile >> 24) & 15;
+    const bool reg = (rows == 1 || rows == 2 || rows == 4 || rows == 8) && (tile >> 12) == 0;
+    const bool tma = (rows == 16 || rows == 32 || rows == 64 || rows == 128) && (tile >> 28) == 0 &&
+                     (ring == 0 || (ring >= 16 && ring <= 192)) && (edges <= 2 || edges == 4 || edges == 8) &&
+                     (cpt <= 2 || cpt == 4);
+    if (tile != 0 && !reg && !tma) return fail(CP_EINVAL, "bad tile (encoding as for cp_sweep_create)");
+    const int t = effective_tile(s->row_tasks[0][0], tile ? tile : make_tile(32, 0, 0, 0));
+    CP_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    s->tile = t;
+    std::vector<GatherTask> all;
+    std::vector<GatherTask *> unused;
+    for (int b = 0; b < 2; ++b) {
+        upload_tasks(s, s->row_tasks[b], unused, all);
+        upload_tasks(s, s->last_tasks[b], unused, all);
+    }
+    CP_CUDA_TRY(cudaMemcpy(s->tasks_dev, all.data(), all.size() * sizeof(GatherTask), cudaMemcpyHostToDevice));
+    return CP_OK;
+}
+
 extern "C" int cp_strip_reset(cp_strip *s) {
     if (!s) return fail(CP_EINVAL, "strip is NULL");
     const size_t row_words = (size_t)s->D1 * s->P;

@@ -224,3 +224,21 @@ def test_wide_rows_eight_chunk_passes():
     want = tm_exact.ptilde("square", 8, 17)
     got = run_strip("square", 8, 17, primes)
     assert got.tolist() == gpu_util.residues_of(want, primes)
+
+
+def test_strip_tiles_agree():
+    # cp_strip_set_tile: the register kernel and TMA geometries give the same residues
+    primes = gpu_util.seed_primes(16, seed=3)
+    want = None
+    for tile in (0, 4, 16 | (48 << 12) | (4 << 20) | (2 << 24), 64 | (64 << 12) | (8 << 20) | (1 << 24),
+                 128 | (32 << 12) | (2 << 20) | (4 << 24)):
+        with cp.Strip("square", 11, primes, max_degree=40, max_rows=8) as s:
+            s.set_tile(tile)
+            s.advance(7)
+            got = s.read().tolist()
+        if want is None:
+            want = got
+        assert got == want, tile
+    with cp.Strip("square", 5, primes, max_degree=8, max_rows=2) as s:
+        with pytest.raises(cp.CPError):
+            s.set_tile(3)
