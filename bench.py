@@ -194,10 +194,12 @@ def table_layout(cp, args):
 
 def tile_name(tile):
     rows, ring, edges, cpt = tile & 0xFFF, (tile >> 12) & 0xFF, (tile >> 20) & 15, (tile >> 24) & 15
+    shape = (tile >> 28) & 3
     if rows <= 8:
         return "register gather kernel, %d rows/warp" % rows
-    return "TMA gather kernel, %d rows/block, %s KB ring, %s edge(s) per stage, %s chunk(s) per thread" % (
-        rows, ring or "auto", edges or "auto", cpt or "auto")
+    return "TMA gather kernel, %d rows/block, %s KB ring, %s edge(s) per stage, %s chunk(s) per thread, %s" % (
+        rows, ring or "auto", edges or "auto", cpt or "auto",
+        {1: "wide blocks", 2: "narrow blocks"}.get(shape, "block shape auto"))
 
 
 def plain_run(cp, torch, lattice, k, primes, stream):

@@ -272,9 +272,14 @@ typedef struct cp_sweep cp_sweep;
 /* tile: 0 = autotune; 1, 2, 4, 8 = register gather kernel, rows per warp;
  *       16, 32, 64, 128 = TMA gather kernel, rows per block, optionally plus
  *       (ring KB << 12) with ring KB in 16..192 (shared-memory ring per block,
- *       0 = 48 KB: four blocks per SM; raised to hold two stages) and
- *       (edges per stage << 20) with 1, 2, 4 or 8 (0 = about 16 KB of source
- *       rows per stage);
+ *       0 = what fills the SM at the kernel's occupancy; raised to hold two
+ *       stages), (edges per stage << 20) with 1, 2, 4 or 8 (0 = about 20 KB
+ *       of source rows per stage, at most 32 / row groups; 4 in narrow blocks), (16-byte chunks
+ *       per consumer thread << 24) with 1, 2 or 4 (0 = 2 for rows wider than
+ *       3 KB, else 1) and (block shape << 28) with 1 = wide (8 / chunks-per-
+ *       thread consumer warps) or 2 = narrow (5 consumer warps; one chunk per
+ *       thread, rows of at most 160 chunks) (0 = narrow where every row of a
+ *       launch has 129..160 chunks at one chunk per thread, else wide);
  * prime_groups: number of strips per width, dividing n_primes, or 0 = autotune.
  * cuda_stream must be a non-default stream (the program is graph-captured on it).
  * Errors: CP_EINVAL (k < 4, k/2 > CP_MAX_L, series longer than 128 terms, bad

@@ -171,22 +171,32 @@ void append_gather_tasks(std::vector<GatherTask> *tasks, const SiteTable &tab, c
 // per block.  For TMA tiles, bits 12..19 = ring size in KB (0: default) and
 // bits 20..23 = edges per stage, 1, 2, 4 or 8 (0: picked from the row size),
 // bits 24..27 = 16-byte chunks per consumer thread, 1, 2 or 4 (0: 2 for rows
-// wider than 3 KB, else 1).  A batch whose rows are not all 16-byte chunked
-// uses the register kernel.
+// wider than 3 KB, else 1), bits 28..29 = consumer block shape, 1 = wide
+// (8 / chunks-per-thread consumer warps), 2 = narrow (5 consumer warps, one
+// chunk per thread, rows of at most 160 chunks), 0 = narrow for batches whose
+// rows all have 129..160 chunks at one chunk per thread, else wide.  A batch
+// whose rows are not all 16-byte chunked uses the register kernel.
 constexpr int kTmaRingKbDefault = 48;
+constexpr int kTileWide = 1 << 28;
+constexpr int kTileNarrow = 2 << 28;
+constexpr int kTmaNarrowWarps = 5;  // consumer warps of a narrow block
 inline int make_tile(int rows, int ring_kb, int edges = 0, int cpt = 0) {
     return rows | (ring_kb << 12) | (edges << 20) | (cpt << 24);
 }
 inline int tile_edges(int tile) { return (tile >> 20) & 15; }
 inline int tile_cpt(int tile) { int c = (tile >> 24) & 15; return c ? c : 1; }
 inline int tile_ring_kb(int tile) { int r = (tile >> 12) & 0xFF; return r ? r : kTmaRingKbDefault; }
+inline int tile_shape(int tile) { return (tile >> 28) & 3; }
 // Blocks per SM the TMA kernel's launch bounds aim at (its registers), and the
-// shared-memory ring that fills the SM at that occupancy.
-__host__ __device__ constexpr int tma_min_blocks(int E, int CPT) {
-    return CPT == 1 ? (E >= 8 ? 3 : 4) : (CPT == 2 ? (E >= 4 ? 4 : 5) : (E >= 4 ? 4 : 5));
+// shared-memory ring that fills the SM at that occupancy; W = consumer warps
+// (0: the wide block, 8 / CPT).
+__host__ __device__ constexpr int tma_min_blocks(int E, int CPT, int W = 0) {
+    return W == kTmaNarrowWarps ? 4
+                                : (CPT == 1 ? (E >= 8 ? 3 : 4) : (CPT == 2 ? 4 : (E >= 4 ? 4 : 5)));
 }
-__host__ __device__ constexpr int tma_ring_kb_for(int E, int CPT) {
-    return tma_min_blocks(E, CPT) <= 3 ? 64 : (tma_min_blocks(E, CPT) == 4 ? 48 : 40);
+__host__ __device__ constexpr int tma_ring_kb_for(int E, int CPT, int W = 0) {
+    return W == kTmaNarrowWarps ? 52
+                                : (tma_min_blocks(E, CPT) <= 3 ? 64 : (tma_min_blocks(E, CPT) == 4 ? 48 : 40));
 }
 bool tile_is_tma(int items);
 bool tma_usable(const GatherTask &t);

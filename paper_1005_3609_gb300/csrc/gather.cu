@@ -145,37 +145,49 @@ uint32_t task_blocks(const GatherTask &t, int items) {
 }
 
 // For TMA tiles: chunks per thread (bits 24..27) default to 2 for rows wider
-// than 3 KB (192 chunks), else 1; edges per stage (bits 20..23) to about 20 KB
-// of rows per stage; the ring (bits 12..19) to what fills the SM at the
+// than 3 KB (192 chunks), else 1; the block shape (bits 28..29) to narrow for
+// rows of 129..160 chunks at one chunk per thread; edges per stage (bits
+// 20..23) to about 20 KB of rows per stage (4 in narrow blocks); the ring
+// (bits 12..19) to what fills the SM at the
 // kernel's occupancy, raised to hold at least two stages of the widest row
 // group.  A batch the TMA kernel cannot take uses the register kernel.
 int effective_tile(const std::vector<GatherTask> &tasks, int items) {
     if (!tile_is_tma(items)) return items & 0xFFF;
-    uint32_t max_rb = 0, max_cw = 0;
+    uint32_t max_rb = 0, max_cw = 0, min_cw = 0xffffffffu;
     for (auto &t : tasks) {
         if (!tma_usable(t)) return kGatherItems;
         max_rb = std::max(max_rb, t.cw * 16u);
         max_cw = std::max(max_cw, t.cw);
+        min_cw = std::min(min_cw, t.cw);
     }
     int cpt = (items >> 24) & 15;
     if (cpt != 1 && cpt != 2 && cpt != 4) cpt = max_cw > 192 ? 2 : 1;
+    // narrow blocks: 5 consumer warps cover rows of 129..160 chunks with at most
+    // 31 idle lanes where the wide block leaves 3 of its 8 warps without a chunk
+    const uint32_t cover = 32u * kTmaNarrowWarps;
+    int shape = tile_shape(items);
+    if (shape != 1 && shape != 2) shape = (cpt == 1 && min_cw > 128 && max_cw <= cover) ? 2 : 1;
+    if (shape == 2 && (cpt != 1 || max_cw > cover)) shape = 1;
     uint32_t max_g = 1;
-    for (auto &t : tasks) {
-        uint32_t G = 1;  // row groups of the kernel's blocks (G * cw <= 256, at most one per consumer warp)
-        while (G < 8u / (uint32_t)cpt && 2 * G * t.cw <= 256) G *= 2;
-        max_g = std::max(max_g, G);
-    }
+    if (shape == 1)
+        for (auto &t : tasks) {
+            uint32_t G = 1;  // row groups of the kernel's blocks (G * cw <= 256, at most one per consumer warp)
+            while (G < 8u / (uint32_t)cpt && 2 * G * t.cw <= 256) G *= 2;
+            max_g = std::max(max_g, G);
+        }
+    // (a narrow block has one row group)
     int edges = tile_edges(items);
     if (edges != 1 && edges != 2 && edges != 4 && edges != 8) {
         const uint32_t per = max_rb ? 20480u / max_rb : 8u;
         edges = per >= 8 ? 8 : (per >= 4 ? 4 : (per >= 2 ? 2 : 1));
+        if (shape == 2) edges = 4;  // narrow blocks: six stages of 4 in the 52 KB ring beat three of 8
     }
     while ((uint32_t)edges * max_g > 32) edges /= 2;  // the producer warp has one lane per group and slot
     int ring = (items >> 12) & 0xFF;
-    if (!ring) ring = tma_ring_kb_for(edges, cpt);
+    if (!ring) ring = tma_ring_kb_for(edges, cpt, shape == 2 ? kTmaNarrowWarps : 0);
     // a row group spans at most 4 KB of slot (G rows of cw chunks, G cw <= 256): two stages need 8 KB per edge
     ring = std::min(192, std::max(ring, std::max(16, 8 * edges)));
-    return make_tile(items & 0xFFF, ring, edges, cpt);
+    return make_tile(items & 0xFFF, ring, edges, cpt) | (shape << 28);
 }
 
 uint32_t assign_blocks(std::vector<GatherTask> &tasks, int items) {
@@ -216,14 +228,14 @@ void append_gather_tasks(std::vector<GatherTask> *tasks, const SiteTable &tab, c
 }
 
 int launch_gather_tma(const GatherTask *tasks_dev, int n_tasks, uint32_t total_blocks, int rpb, int *err,
-                      cudaStream_t st, int edges, int ring_kb, int cpt);
+                      cudaStream_t st, int edges, int ring_kb, int cpt, bool narrow);
 int prepare_gather_tma();
 
 int launch_gather(const GatherTask *tasks_dev, int n_tasks, uint32_t total_blocks, int items, cudaStream_t st) {
     if (n_tasks <= 0 || total_blocks == 0) return CP_OK;
     if (tile_is_tma(items))
         return launch_gather_tma(tasks_dev, n_tasks, total_blocks, items & 0xFFE, device_error_flag(), st,
-                                 tile_edges(items), tile_ring_kb(items), tile_cpt(items));
+                                 tile_edges(items), tile_ring_kb(items), tile_cpt(items), tile_shape(items) == 2);
     switch (items & 0xFFF) {
         case 1: gather_kernel<1><<<total_blocks, kGatherThreads, 0, st>>>(tasks_dev, n_tasks); break;
         case 2: gather_kernel<2><<<total_blocks, kGatherThreads, 0, st>>>(tasks_dev, n_tasks); break;

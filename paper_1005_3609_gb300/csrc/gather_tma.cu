@@ -17,10 +17,12 @@
 // mbarrier (one arrival per consumer warp of the group): consumers wait once
 // per stage, not once per edge.
 //
-// Warps 1..8 are the consumers, 8/G per group, one 16-byte chunk (four primes
-// of one degree) per thread; warps whose chunks all lie beyond the row leave at
-// once.  Per stage a consumer loads its E chunks into registers, releases the
-// stage, then adds coef * chunk into signed 64-bit accumulators edge by edge;
+// Warps 1..W are the consumers, W/G per group, CPT 16-byte chunks (four primes
+// of one degree each) per thread: W = 8 / CPT (a wide block, 256 chunks), or
+// W = 5 at CPT 1 (a narrow block for rows of 129..160 chunks, one group);
+// warps whose chunks all lie beyond the row leave at once.  Per stage a
+// consumer reads the E coefficients, then edge by edge its chunks of the slots,
+// adding coef * chunk into signed 64-bit accumulators, and releases the stage;
 // when the CSR reaches the end of a destination row the thread reduces its four
 // words modulo their primes (integer Barrett, modred.cuh) and streams them out.
 //
@@ -347,14 +349,16 @@ __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock 
     }
 }
 
-__host__ __device__ constexpr int tma_threads(int CPT) { return 32 * (1 + kTmaConsumers / CPT); }
+__host__ __device__ constexpr int tma_threads(int W) { return 32 * (1 + W); }
 
-template <int E, int CPT>
-__global__ void __launch_bounds__(tma_threads(CPT), tma_min_blocks(E, CPT))
+// W consumer warps: 8 / CPT (the wide block, 256 chunks per block) or
+// kTmaNarrowWarps at CPT 1 (160 chunks, one row group).
+template <int E, int CPT, int W>
+__global__ void __launch_bounds__(tma_threads(W), tma_min_blocks(E, CPT, W == kTmaConsumers / CPT ? 0 : W))
     gather_tma_kernel(const GatherTask *__restrict__ tasks, int n_tasks, uint32_t rpb, uint32_t ring_bytes, int *err) {
     extern __shared__ __align__(128) uint8_t ring[];
     __shared__ TmaShared S;
-    constexpr uint32_t W = kTmaConsumers / CPT;  // consumer warps
+    constexpr uint32_t kCover = 32u * W * CPT;  // chunks one block covers
 
     if (threadIdx.x == 0) S.abort_flag = *(volatile int *)err;  // a previous block gave up: do nothing
     __syncthreads();
@@ -372,13 +376,13 @@ __global__ void __launch_bounds__(tma_threads(CPT), tma_min_blocks(E, CPT))
     bk.row0 = (b - t.block_begin) * rpb;
     bk.nrows = min(rpb, t.rows - bk.row0);
     const uint32_t RB = t.cw * 16u;
-    bk.G = 1;  // row groups: each group's warps cover 256 / G chunks
-    while (bk.G < W && 2 * bk.G * t.cw <= 256) bk.G *= 2;
+    bk.G = 1;  // row groups: each group's warps cover kCover / G chunks (G divides W)
+    while (W % (2 * bk.G) == 0 && 2 * bk.G * t.cw <= kCover) bk.G *= 2;
     const uint32_t slots_g = min((uint32_t)kTmaMaxSlots / bk.G, ring_bytes / (bk.G * RB));
     bk.NS = slots_g / E;                                 // stages per group
     const uint32_t wpg = W / bk.G;                       // consumer warps per group
     bk.act = min(wpg, (t.cw + 31) / 32);                 // warps with chunks, per group
-    if (bk.NS == 0 || bk.G * E > 32 || t.cw > 256 || t.cw == 0 || rpb > (uint32_t)kTmaMaxRows) {  // refusal
+    if (bk.NS == 0 || bk.G * E > 32 || t.cw > kCover || t.cw == 0 || rpb > (uint32_t)kTmaMaxRows) {  // refusal
         if (threadIdx.x == 0) atomicOr(err, 8);
         return;
     }
@@ -421,18 +425,18 @@ constexpr uint32_t kTmaRingMin = 16 * 1024;
 
 bool tma_usable(const GatherTask &t) { return t.vec4 && t.cw >= 1 && t.cw <= 256; }
 
-template <int E, int CPT>
+template <int E, int CPT, int W>
 static int set_attr() {
-    CP_CUDA_TRY(cudaFuncSetAttribute(gather_tma_kernel<E, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CP_CUDA_TRY(cudaFuncSetAttribute(gather_tma_kernel<E, CPT, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kTmaRingMax));
     return CP_OK;
 }
 
-template <int CPT>
+template <int CPT, int W>
 static int set_attrs() {
     int rc;
-    if ((rc = set_attr<1, CPT>()) || (rc = set_attr<2, CPT>()) || (rc = set_attr<4, CPT>()) ||
-        (rc = set_attr<8, CPT>()))
+    if ((rc = set_attr<1, CPT, W>()) || (rc = set_attr<2, CPT, W>()) || (rc = set_attr<4, CPT, W>()) ||
+        (rc = set_attr<8, CPT, W>()))
         return rc;
     return CP_OK;
 }
@@ -460,29 +464,32 @@ int prepare_gather_tma() {
     if (dev < 0 || dev >= 64) return fail(CP_EINVAL, "device index");
     if (done[dev]) return CP_OK;
     int rc;
-    if ((rc = set_attrs<1>()) || (rc = set_attrs<2>()) || (rc = set_attrs<4>())) return rc;
+    if ((rc = set_attrs<1, kTmaConsumers>()) || (rc = set_attrs<2, kTmaConsumers / 2>()) ||
+        (rc = set_attrs<4, kTmaConsumers / 4>()) || (rc = set_attrs<1, kTmaNarrowWarps>()))
+        return rc;
     done[dev] = true;
     return CP_OK;
 }
 
-template <int CPT>
+template <int CPT, int W>
 static int launch_cpt(const GatherTask *tasks_dev, int n_tasks, uint32_t blocks, uint32_t rpb, uint32_t dyn, int *err,
                       cudaStream_t st, int edges) {
-    constexpr int T = tma_threads(CPT);
+    constexpr int T = tma_threads(W);
     switch (edges) {
-        case 1: gather_tma_kernel<1, CPT><<<blocks, T, dyn, st>>>(tasks_dev, n_tasks, rpb, dyn, err); break;
-        case 2: gather_tma_kernel<2, CPT><<<blocks, T, dyn, st>>>(tasks_dev, n_tasks, rpb, dyn, err); break;
-        case 4: gather_tma_kernel<4, CPT><<<blocks, T, dyn, st>>>(tasks_dev, n_tasks, rpb, dyn, err); break;
-        case 8: gather_tma_kernel<8, CPT><<<blocks, T, dyn, st>>>(tasks_dev, n_tasks, rpb, dyn, err); break;
+        case 1: gather_tma_kernel<1, CPT, W><<<blocks, T, dyn, st>>>(tasks_dev, n_tasks, rpb, dyn, err); break;
+        case 2: gather_tma_kernel<2, CPT, W><<<blocks, T, dyn, st>>>(tasks_dev, n_tasks, rpb, dyn, err); break;
+        case 4: gather_tma_kernel<4, CPT, W><<<blocks, T, dyn, st>>>(tasks_dev, n_tasks, rpb, dyn, err); break;
+        case 8: gather_tma_kernel<8, CPT, W><<<blocks, T, dyn, st>>>(tasks_dev, n_tasks, rpb, dyn, err); break;
         default: return fail(CP_EINVAL, "TMA gather edges per stage must be 1, 2, 4 or 8");
     }
     return CP_OK;
 }
 
 // rpb: destination rows per block (16..128); edges: edges per stage (1, 2, 4 or 8);
-// cpt: 16-byte chunks per consumer thread (1, 2 or 4); ring_kb: shared-memory ring per block.
+// cpt: 16-byte chunks per consumer thread (1, 2 or 4); ring_kb: shared-memory ring per block;
+// narrow: 5 consumer warps (cpt 1, rows of at most 160 chunks) instead of 8 / cpt.
 int launch_gather_tma(const GatherTask *tasks_dev, int n_tasks, uint32_t total_blocks, int rpb, int *err,
-                      cudaStream_t st, int edges, int ring_kb, int cpt) {
+                      cudaStream_t st, int edges, int ring_kb, int cpt, bool narrow) {
     if (n_tasks <= 0 || total_blocks == 0) return CP_OK;
     if (rpb != 16 && rpb != 32 && rpb != 64 && rpb != 128)
         return fail(CP_EINVAL, "TMA gather rows per block must be 16, 32, 64 or 128");
@@ -490,10 +497,14 @@ int launch_gather_tma(const GatherTask *tasks_dev, int n_tasks, uint32_t total_b
     if (dyn < kTmaRingMin) dyn = kTmaRingMin;
     if (dyn > kTmaRingMax) dyn = kTmaRingMax;
     int rc;
+    if (narrow && cpt != 1) return fail(CP_EINVAL, "narrow TMA gather blocks take one chunk per thread");
     switch (cpt) {
-        case 1: rc = launch_cpt<1>(tasks_dev, n_tasks, total_blocks, rpb, dyn, err, st, edges); break;
-        case 2: rc = launch_cpt<2>(tasks_dev, n_tasks, total_blocks, rpb, dyn, err, st, edges); break;
-        case 4: rc = launch_cpt<4>(tasks_dev, n_tasks, total_blocks, rpb, dyn, err, st, edges); break;
+        case 1:
+            rc = narrow ? launch_cpt<1, kTmaNarrowWarps>(tasks_dev, n_tasks, total_blocks, rpb, dyn, err, st, edges)
+                        : launch_cpt<1, kTmaConsumers>(tasks_dev, n_tasks, total_blocks, rpb, dyn, err, st, edges);
+            break;
+        case 2: rc = launch_cpt<2, kTmaConsumers / 2>(tasks_dev, n_tasks, total_blocks, rpb, dyn, err, st, edges); break;
+        case 4: rc = launch_cpt<4, kTmaConsumers / 4>(tasks_dev, n_tasks, total_blocks, rpb, dyn, err, st, edges); break;
         default: return fail(CP_EINVAL, "TMA gather chunks per thread must be 1, 2 or 4");
     }
     if (rc) return rc;

@@ -355,7 +355,7 @@ extern "C" int cp_strip_set_tile(cp_strip *s, int tile) {
     if (!s) return fail(CP_EINVAL, "strip is NULL");
     const int rows = tile & 0xFFF, ring = (tile >> 12) & 0xFF, edges = (tile >> 20) & 15, cpt = (tile >> 24) & 15;
     const bool reg = (rows == 1 || rows == 2 || rows == 4 || rows == 8) && (tile >> 12) == 0;
-    const bool tma = (rows == 16 || rows == 32 || rows == 64 || rows == 128) && (tile >> 28) == 0 &&
+    const bool tma = (rows == 16 || rows == 32 || rows == 64 || rows == 128) && (tile >> 30) == 0 && tile_shape(tile) != 3 &&
                      (ring == 0 || (ring >= 16 && ring <= 192)) && (edges <= 2 || edges == 4 || edges == 8) &&
                      (cpt <= 2 || cpt == 4);
     if (tile != 0 && !reg && !tma) return fail(CP_EINVAL, "bad tile (encoding as for cp_sweep_create)");

@@ -308,14 +308,14 @@ extern "C" int cp_sweep_create(int lattice, int k, const uint32_t *primes, int n
         const int rows = tile & 0xFFF, ring = (tile >> 12) & 0xFF, edges = (tile >> 20) & 15,
                   cpt = (tile >> 24) & 15;
         const bool reg = (rows == 1 || rows == 2 || rows == 4 || rows == 8) && (tile >> 12) == 0;
-        const bool tma = (rows == 16 || rows == 32 || rows == 64 || rows == 128) && (tile >> 28) == 0 &&
+        const bool tma = (rows == 16 || rows == 32 || rows == 64 || rows == 128) && (tile >> 30) == 0 && tile_shape(tile) != 3 &&
                          (cpt <= 2 || cpt == 4) &&
                          (ring == 0 || (ring >= 16 && ring <= 192)) &&
                          (edges <= 2 || edges == 4 || edges == 8);
         if (tile != 0 && !reg && !tma)
             return fail(CP_EINVAL, "tile must be 0 (autotune), 1, 2, 4, 8 (register kernel) or 16, 32, 64, 128 "
                                    "(TMA) + (ring KB 16..192 << 12) + (edges per stage 1, 2, 4, 8 << 20) + "
-                                   "(chunks per thread 1, 2, 4 << 24)");
+                                   "(chunks per thread 1, 2, 4 << 24) + (block shape 1 wide, 2 narrow << 28)");
     }
     if (prime_groups < 0 || (prime_groups > 0 && n_primes % prime_groups != 0))
         return fail(CP_EINVAL, "prime_groups must divide n_primes");
@@ -337,7 +337,8 @@ extern "C" int cp_sweep_create(int lattice, int k, const uint32_t *primes, int n
     std::vector<int> tiles = tile ? std::vector<int>{tile}
                                   : std::vector<int>{make_tile(32, 0, 0, 0), make_tile(64, 0, 0, 0),
                                                      make_tile(32, 48, 4, 2), make_tile(64, 48, 4, 2),
-                                                     make_tile(32, 64, 8, 1), make_tile(64, 64, 8, 1),
+                                                     make_tile(32, 64, 8, 1) | kTileWide,
+                                                     make_tile(64, 64, 8, 1) | kTileWide,
                                                      make_tile(16, 0, 0, 0), 4};
     std::vector<int> grps;
     if (prime_groups) grps = {prime_groups};

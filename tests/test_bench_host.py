@@ -75,3 +75,5 @@ def test_tile_names():
     assert bench.tile_name(4) == "register gather kernel, 4 rows/warp"
     assert "32 rows/block, 40 KB ring, 2 edge(s) per stage, 2 chunk(s) per thread" in bench.tile_name(
         32 | (40 << 12) | (2 << 20) | (2 << 24))
+    assert bench.tile_name(64 | (8 << 20) | (2 << 28)).endswith("narrow blocks")
+    assert bench.tile_name(64 | (1 << 28)).endswith("wide blocks")

@@ -242,3 +242,22 @@ def test_strip_tiles_agree():
     with cp.Strip("square", 5, primes, max_degree=8, max_rows=2) as s:
         with pytest.raises(cp.CPError):
             s.set_tile(3)
+        with pytest.raises(cp.CPError):
+            s.set_tile(32 | (3 << 28))  # no block shape 3
+
+
+@pytest.mark.parametrize("lattice", ["square", "triangular"])
+def test_narrow_blocks_match_oracle(lattice):
+    # 6 x 6 at full degree with 16 primes: rows of 36 degrees x 4 chunks = 144
+    # chunks, which the default tile gathers with narrow blocks (5 consumer
+    # warps); narrow blocks at every stage size and the forced wide block give
+    # the oracle's residues
+    primes = gpu_util.seed_primes(16, seed=11)
+    want = gpu_util.residues_of(tm_exact.ptilde(lattice, 6, 6), primes)
+    narrow, wide = 2 << 28, 1 << 28
+    for tile in (0, 16 | (1 << 20) | narrow, 32 | (2 << 20) | (1 << 24) | narrow, 64 | (4 << 20) | narrow,
+                 128 | (8 << 20) | (52 << 12) | narrow, 64 | (8 << 20) | (1 << 24) | wide, 32 | narrow | (2 << 24)):
+        with cp.Strip(lattice, 6, primes, max_degree=-1, max_rows=6) as s:
+            s.set_tile(tile)
+            s.advance(5)
+            assert s.read().tolist() == want, hex(tile)
