@@ -102,6 +102,7 @@ struct SiteTable {
     uint64_t n_site_out = 0;  // output states of the per-site factors it stands for (n_dst, or mid + n_dst)
     uint32_t *row_ptr = nullptr;  // [n_dst + 1]
     uint32_t *edges = nullptr;    // [nnz]
+    uint32_t *block_order = nullptr;  // row blocks by smallest source (GatherTask::block_order), or null
 };
 
 // All tables of one (lattice, L) on one device; shared between strips.
@@ -156,8 +157,18 @@ struct GatherTask {
     uint32_t c0;              // first chunk of the rows handled by this task
     uint32_t cw;              // chunks handled (a column range [c0, c0 + cw) of every row)
     uint32_t src_bits;        // edge format of the table
-    uint32_t pad[2];
+    // TMA kernel: the order in which its blocks visit the row blocks, for 16,
+    // 32, 64 and 128 rows per block one after another (block_order_offset),
+    // or null for row-block order
+    const uint32_t *block_order;
 };
+
+// Start of the order for `rpb` rows per block in a table of `rows` rows.
+__host__ __device__ inline uint32_t block_order_offset(uint32_t rows, uint32_t rpb) {
+    uint32_t off = 0;
+    for (uint32_t l = 16; l < rpb; l *= 2) off += (rows + l - 1) / l;
+    return off;
+}
 
 constexpr int kGatherThreads = 256;  // 8 warps; one warp per destination row at a time
 constexpr int kGatherItems = 4;      // default rows per warp (the tile: 8 * rows per block)

@@ -219,6 +219,7 @@ void append_gather_tasks(std::vector<GatherTask> *tasks, const SiteTable &tab, c
     t.magic_cpd = magic_for(t.cpd);
     t.n_primes = (uint32_t)P;
     t.src_bits = (uint32_t)tab.op.src_bits;
+    t.block_order = tab.block_order;
     const uint32_t ncol = v4 ? (t.C + 255) / 256 : 1;
     for (uint32_t k = 0; k < ncol; ++k) {  // balanced column ranges
         t.c0 = (uint32_t)((uint64_t)t.C * k / ncol);

@@ -373,7 +373,9 @@ __global__ void __launch_bounds__(tma_threads(W), tma_min_blocks(E, CPT, W == kT
     __syncthreads();
     const GatherTask &t = S.task;
     TmaBlock bk;
-    bk.row0 = (b - t.block_begin) * rpb;
+    uint32_t rb = b - t.block_begin;  // row block of this block
+    if (t.block_order) rb = __ldg(t.block_order + block_order_offset(t.rows, rpb) + rb);
+    bk.row0 = rb * rpb;
     bk.nrows = min(rpb, t.rows - bk.row0);
     const uint32_t RB = t.cw * 16u;
     bk.G = 1;  // row groups: each group's warps cover kCover / G chunks (G divides W)

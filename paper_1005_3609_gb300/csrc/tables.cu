@@ -9,6 +9,7 @@
 // and shared by every strip, row, height and prime.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -446,6 +447,59 @@ int build_x_prefix(int m, int e, cudaStream_t st, uint32_t **out) {
     return CP_OK;
 }
 
+// Smallest source state of each row block of `rpb` destination rows (one warp
+// per block; a block without edges gets 0xffffffff).
+__global__ void block_min_src_kernel(const uint32_t *row_ptr, const uint32_t *edges, uint32_t n_dst, uint32_t mask,
+                                     uint32_t rpb, uint32_t nb, uint32_t *key) {
+    const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (w >= nb) return;
+    const uint32_t r0 = w * rpb, r1 = min(n_dst, r0 + rpb);
+    const uint32_t e1 = row_ptr[r1];
+    uint32_t m = 0xffffffffu;
+    for (uint32_t e = row_ptr[r0] + lane; e < e1; e += 32) m = min(m, edges[e] & mask);
+    m = __reduce_min_sync(0xffffffffu, m);
+    if (lane == 0) key[w] = m;
+}
+
+constexpr uint64_t kBlockOrderMinRows = 4096;  // smaller tables keep row-block order
+
+// The order in which the TMA gather's blocks visit a table's row blocks: by
+// the smallest source state a row block reads (ties in row order), for each
+// rows-per-block choice.  Destinations whose sources lie close together then
+// run at the same time, so a source row fetched into L2 serves the blocks that
+// need it before it is evicted -- the factors of the first sites of a row draw
+// their sources from the whole state vector in rank order.  Any order gives
+// the same results; this one only changes DRAM traffic.
+static int build_block_order(SiteTable *tab, cudaStream_t st) {
+    if (tab->n_dst < kBlockOrderMinRows || tab->nnz == 0) return CP_OK;
+    const uint32_t n = (uint32_t)tab->n_dst;
+    const uint32_t total = block_order_offset(n, 256);  // 16, 32, 64 and 128 rows per block
+    uint32_t *key = nullptr;
+    int rc = dev_alloc((void **)&key, (size_t)total * 4);
+    if (rc) return rc;
+    const uint32_t mask = (1u << tab->op.src_bits) - 1u;
+    for (uint32_t l = 16; l <= 128; l *= 2) {
+        const uint32_t nb = (n + l - 1) / l;
+        block_min_src_kernel<<<(nb + 7) / 8, 256, 0, st>>>(tab->row_ptr, tab->edges, n, mask, l, nb,
+                                                           key + block_order_offset(n, l));
+    }
+    std::vector<uint32_t> hk(total), order(total);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hk.data(), key, (size_t)total * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    dev_free(key);
+    if (e != cudaSuccess) return fail(CP_ECUDA, std::string("block order: ") + cudaGetErrorString(e));
+    for (uint32_t l = 16; l <= 128; l *= 2) {
+        const uint32_t off = block_order_offset(n, l), nb = (n + l - 1) / l;
+        uint32_t *o = order.data() + off;
+        for (uint32_t i = 0; i < nb; ++i) o[i] = i;
+        std::stable_sort(o, o + nb, [&](uint32_t a, uint32_t b) { return hk[off + a] < hk[off + b]; });
+    }
+    if ((rc = dev_alloc((void **)&tab->block_order, (size_t)total * 4))) return rc;
+    CP_CUDA_TRY(cudaMemcpy(tab->block_order, order.data(), (size_t)total * 4, cudaMemcpyHostToDevice));
+    return CP_OK;
+}
+
 static int build_table(const OpDesc &op, const RankTables *T_dev, cudaStream_t st, SiteTable *tab) {
     tab->op = op;
     tab->n_src = op.in.size;
@@ -536,7 +590,7 @@ static int build_table(const OpDesc &op, const RankTables *T_dev, cudaStream_t s
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cleanup();
     if (e != cudaSuccess) return fail(CP_ECUDA, std::string("csr fill: ") + cudaGetErrorString(e));
-    return CP_OK;
+    return build_block_order(tab, st);
 }
 
 TableSet::~TableSet() {
@@ -544,10 +598,12 @@ TableSet::~TableSet() {
     for (auto &t : row) {
         dev_free(t.row_ptr);
         dev_free(t.edges);
+        dev_free(t.block_order);
     }
     for (auto &t : last) {
         dev_free(t.row_ptr);
         dev_free(t.edges);
+        dev_free(t.block_order);
     }
 }
 
