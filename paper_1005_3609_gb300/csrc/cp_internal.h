@@ -157,6 +157,8 @@ struct GatherTask {
     uint32_t c0;              // first chunk of the rows handled by this task
     uint32_t cw;              // chunks handled (a column range [c0, c0 + cw) of every row)
     uint32_t src_bits;        // edge format of the table
+    uint32_t partial;         // 1: the output feeds further gathers only (words may be left in [-p, p))
+    uint32_t pad;
     // TMA kernel: the order in which its blocks visit the row blocks, for 16,
     // 32, 64 and 128 rows per block one after another (block_order_offset),
     // or null for row-block order
@@ -175,8 +177,11 @@ constexpr int kGatherItems = 4;      // default rows per warp (the tile: 8 * row
 
 // Append the task(s) of one per-site factor: rows of 16-byte chunks wider than
 // 256 chunks are split into column tasks of at most 256 chunks each.
+// partial: the output vector is read by further gathers only, so the TMA kernel
+// may store signed representatives in [-p, p) (every gather reads its input
+// words as signed 32-bit values).
 void append_gather_tasks(std::vector<GatherTask> *tasks, const SiteTable &tab, const uint32_t *in,
-                         uint32_t *out, const uint32_t *primes_dev, int D1, int P);
+                         uint32_t *out, const uint32_t *primes_dev, int D1, int P, bool partial = false);
 // Gather tile (low 12 bits): 1, 2, 4, 8 = register kernel with that many rows
 // per warp (8 warps per block); 16, 32, 64, 128 = TMA kernel with that many rows
 // per block.  For TMA tiles, bits 12..19 = ring size in KB (0: default) and

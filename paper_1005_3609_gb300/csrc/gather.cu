@@ -203,7 +203,7 @@ uint32_t assign_blocks(std::vector<GatherTask> &tasks, int items) {
 static uint32_t magic_for(uint32_t d) { return d <= 1 ? 0u : (uint32_t)(((1ull << 32) + d - 1) / d); }
 
 void append_gather_tasks(std::vector<GatherTask> *tasks, const SiteTable &tab, const uint32_t *in, uint32_t *out,
-                         const uint32_t *primes_dev, int D1, int P) {
+                         const uint32_t *primes_dev, int D1, int P, bool partial) {
     const bool v4 = (P % 4) == 0;
     const uint32_t vec = v4 ? 4 : 1;
     GatherTask t{};
@@ -220,6 +220,7 @@ void append_gather_tasks(std::vector<GatherTask> *tasks, const SiteTable &tab, c
     t.n_primes = (uint32_t)P;
     t.src_bits = (uint32_t)tab.op.src_bits;
     t.block_order = tab.block_order;
+    t.partial = partial ? 1u : 0u;
     const uint32_t ncol = v4 ? (t.C + 255) / 256 : 1;
     for (uint32_t k = 0; k < ncol; ++k) {  // balanced column ranges
         t.c0 = (uint32_t)((uint64_t)t.C * k / ncol);

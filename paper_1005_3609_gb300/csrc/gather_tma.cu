@@ -236,7 +236,7 @@ __device__ __forceinline__ void stcs128_if(uint4 *ptr, uint4 v, uint32_t pred) {
 // and not stored.  PRED: the warp holds chunks of degree < kTmaMaxShift (only
 // the first chunk can), where a shifted copy leaves the slot's low chunks
 // unwritten and the shift must be checked.
-template <int E, int CPT, bool PRED>
+template <int E, int CPT, bool PRED, bool FULL>
 __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock &bk, TmaShared &S, uint32_t ring_addr,
                                             uint32_t g, uint32_t c, uint32_t stride, int *err) {
     const uint32_t lane = threadIdx.x & 31;
@@ -287,10 +287,14 @@ __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock 
                 m = *reinterpret_cast<const uint4 *>(S.m + pcs[k]);
                 sh = *reinterpret_cast<const uint4 *>(S.s + pcs[k]);
             }
-            stcs128_if(out + (size_t)r * C + gcs[k],
-                       make_uint4(modred_reduce(a[k][0], p.x, m.x, sh.x), modred_reduce(a[k][1], p.y, m.y, sh.y),
-                                  modred_reduce(a[k][2], p.z, m.z, sh.z), modred_reduce(a[k][3], p.w, m.w, sh.w)),
-                       active[k]);
+            const uint4 v =
+                FULL ? make_uint4(modred_reduce(a[k][0], p.x, m.x, sh.x), modred_reduce(a[k][1], p.y, m.y, sh.y),
+                                  modred_reduce(a[k][2], p.z, m.z, sh.z), modred_reduce(a[k][3], p.w, m.w, sh.w))
+                     : make_uint4(modred_reduce_signed(a[k][0], p.x, m.x, sh.x),
+                                  modred_reduce_signed(a[k][1], p.y, m.y, sh.y),
+                                  modred_reduce_signed(a[k][2], p.z, m.z, sh.z),
+                                  modred_reduce_signed(a[k][3], p.w, m.w, sh.w));
+            stcs128_if(out + (size_t)r * C + gcs[k], v, active[k]);
         }
         ++r;
         reset();
@@ -415,10 +419,14 @@ __global__ void __launch_bounds__(tma_threads(W), tma_min_blocks(E, CPT, W == kT
     const uint32_t c = wi * 32 + (threadIdx.x & 31);
     const uint32_t stride = 32 * wpg;  // chunks the group's warps cover side by side
     const uint32_t ring_addr = smem_addr(ring);
-    if (t.c0 + wi * 32 < (uint32_t)kTmaMaxShift * t.cpd)
-        tma_consume<E, CPT, true>(t, bk, S, ring_addr, g, c, stride, err);
-    else
-        tma_consume<E, CPT, false>(t, bk, S, ring_addr, g, c, stride, err);
+    const bool pred = t.c0 + wi * 32 < (uint32_t)kTmaMaxShift * t.cpd;
+    if (t.partial) {
+        if (pred) tma_consume<E, CPT, true, false>(t, bk, S, ring_addr, g, c, stride, err);
+        else tma_consume<E, CPT, false, false>(t, bk, S, ring_addr, g, c, stride, err);
+    } else {
+        if (pred) tma_consume<E, CPT, true, true>(t, bk, S, ring_addr, g, c, stride, err);
+        else tma_consume<E, CPT, false, true>(t, bk, S, ring_addr, g, c, stride, err);
+    }
 }
 
 // Ring sizes: ring_kb KB per block (several blocks per SM).

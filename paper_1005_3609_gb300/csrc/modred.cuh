@@ -1,6 +1,7 @@
 // Exact reduction of a gather accumulator modulo a prime, integer arithmetic only.
 //
-// A destination word accumulates v = sum_e coef_e x_e with 0 <= x_e < p, so
+// A destination word accumulates v = sum_e coef_e x_e with |x_e| < p (inputs
+// are residues in [0, p) or signed representatives in [-p, p)), so
 // |v| < p S where S = sum_e |coef_e| over the destination's edges; the table
 // build refuses any table with S >= 2^20 (kReduceMaxCoefSum).  Arithmetic is
 // modulo primes below 2^31 (Sec. 3.5).
@@ -49,6 +50,18 @@ __host__ __device__ __forceinline__ ModRed modred_make(uint32_t p) {
 
 // The bias every accumulator of prime p starts from: p 2^21.
 __host__ __device__ __forceinline__ long long modred_bias(uint32_t p) { return (long long)p << 21; }
+
+// A signed representative of u mod p in [-p, p), as its 32-bit two's
+// complement: r - p with r = u - q p in [0, 2p) (one instruction fewer than
+// the full reduction).  The gathers read every input word as a signed 32-bit
+// value, so inputs in [-p, p) still give |v| < p S and the bias above covers
+// them; a gather whose output only feeds further gathers may store this.
+__device__ __forceinline__ uint32_t modred_reduce_signed(long long acc, uint32_t p, uint32_t m, uint32_t s) {
+    const unsigned long long u = (unsigned long long)acc;
+    const uint32_t h = (uint32_t)(u >> s);
+    const uint32_t q = __umulhi(h, m);
+    return (uint32_t)u - q * p - p;  // r - p, r in [0, 2p); exact modulo 2^32
+}
 
 // u mod p for an accumulator u = p 2^21 + v, |v| < p 2^20.
 __device__ __forceinline__ uint32_t modred_reduce(long long acc, uint32_t p, uint32_t m, uint32_t s) {

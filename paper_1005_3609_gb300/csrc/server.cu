@@ -216,6 +216,7 @@ static bool next_tasks(Job *j, std::vector<GatherTask> *tasks, uint64_t *upd) {
     const SiteTable *tab;
     const uint32_t *in;
     uint32_t *out;
+    bool partial = true;  // every output but the result feeds further gathers only
     if (j->op < main_ops) {
         const int i = j->op % nrow;
         tab = &ts.row[i];
@@ -225,9 +226,10 @@ static bool next_tasks(Job *j, std::vector<GatherTask> *tasks, uint64_t *upd) {
         const int k = j->op - main_ops;
         tab = &ts.last[k];
         in = k == 0 ? j->vec[main_ops & 1] : j->scratch[(k - 1) & 1];
-        out = (k + 1 == (int)ts.last.size()) ? j->row : j->scratch[k & 1];
+        partial = k + 1 < (int)ts.last.size();
+        out = partial ? j->scratch[k & 1] : j->row;
     }
-    append_gather_tasks(tasks, *tab, in, out, j->primes_dev, j->D1, j->P);
+    append_gather_tasks(tasks, *tab, in, out, j->primes_dev, j->D1, j->P, partial);
     // updates count the requested primes only (padding lanes are not work asked for)
     int real = 0;
     for (auto &m : j->members) real += m.first->P;

@@ -177,7 +177,7 @@ static int make_strip(std::shared_ptr<TableSet> tabs, int lattice, int L, const 
         int cur = b;
         for (size_t i = 0; i < ts.row.size(); ++i) {
             std::vector<GatherTask> l;
-            append_gather_tasks(&l, ts.row[i], s->vec[cur], s->vec[cur ^ 1], s->primes_dev, s->D1, s->P);
+            append_gather_tasks(&l, ts.row[i], s->vec[cur], s->vec[cur ^ 1], s->primes_dev, s->D1, s->P, true);
             s->row_tasks[b].push_back(l);
             cur ^= 1;
         }
@@ -185,7 +185,8 @@ static int make_strip(std::shared_ptr<TableSet> tabs, int lattice, int L, const 
         int sc = 0;
         for (size_t i = 0; i < ts.last.size(); ++i) {
             std::vector<GatherTask> l;
-            append_gather_tasks(&l, ts.last[i], src, s->scratch[sc], s->primes_dev, s->D1, s->P);
+            append_gather_tasks(&l, ts.last[i], src, s->scratch[sc], s->primes_dev, s->D1, s->P,
+                                i + 1 < ts.last.size());
             s->last_tasks[b].push_back(l);
             src = s->scratch[sc];
             sc ^= 1;

@@ -169,7 +169,7 @@ static int build_program(cp_sweep *sw, int tile) {
         for (int row = 0; row < smax - 1; ++row)
             for (int i = 0; i < nf; ++i) {
                 const size_t t = (size_t)row * nf + i;
-                append_gather_tasks(&at(t), ts.row[i], st.vec[t & 1], st.vec[(t & 1) ^ 1], pr, sw->D1, Pg);
+                append_gather_tasks(&at(t), ts.row[i], st.vec[t & 1], st.vec[(t & 1) ^ 1], pr, sw->D1, Pg, true);
                 count_work(sw, ts.row[i], Pg);
             }
         // read-out lanes
@@ -181,7 +181,7 @@ static int build_program(cp_sweep *sw, int tile) {
             for (size_t i = 0; i < ts.last.size(); ++i) {
                 const bool final = i + 1 == ts.last.size();
                 uint32_t *dst = final ? slot : st.scratch[sc];
-                append_gather_tasks(&at(t0 + i), ts.last[i], src, dst, pr, sw->D1, Pg);
+                append_gather_tasks(&at(t0 + i), ts.last[i], src, dst, pr, sw->D1, Pg, !final);
                 count_work(sw, ts.last[i], Pg);
                 src = dst;
                 sc ^= 1;
