@@ -130,8 +130,9 @@ int cp_strip_info(const cp_strip *s, uint64_t n_states[2], int *degree, int *hei
 int cp_strip_work(const cp_strip *s, uint64_t work[6]);
 
 /* Gather tile of the strip's launches, encoded as cp_sweep_create's tile
- * (0 = the default: TMA kernel, 32 rows per block, stages, chunks per thread
- * and ring picked from the row width).  A tuning knob: results are identical
+ * (0 = the default: TMA kernel, 32 rows per block -- 16 where 32-row blocks
+ * would give a launch fewer than eight waves of resident blocks -- stages,
+ * chunks per thread and ring picked from the row width).  A tuning knob: results are identical
  * for every tile.  Synchronises the strip's stream.  CP_EINVAL on a bad tile. */
 int cp_strip_set_tile(cp_strip *s, int tile);
 

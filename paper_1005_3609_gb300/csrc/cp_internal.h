@@ -221,6 +221,8 @@ uint32_t task_blocks(const GatherTask &t, int items);
 uint32_t assign_blocks(std::vector<GatherTask> &tasks, int items);
 // Effective tile for a batch (falls back from TMA to the register kernel when needed).
 int effective_tile(const std::vector<GatherTask> &tasks, int items);
+// Rows per block of the default TMA tile for a launch of these tasks (16 or 32).
+int default_rows(const std::vector<GatherTask> &tasks);
 // Launch a batch of tasks (tasks_dev = device copy, block_begin assigned for `items`).
 int launch_gather(const GatherTask *tasks_dev, int n_tasks, uint32_t total_blocks, int items, cudaStream_t st);
 // Set the kernels' shared-memory attributes (call outside stream capture).

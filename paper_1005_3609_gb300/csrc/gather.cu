@@ -190,6 +190,20 @@ int effective_tile(const std::vector<GatherTask> &tasks, int items) {
     return make_tile(items & 0xFFF, ring, edges, cpt) | (shape << 28);
 }
 
+// Rows per block of the default TMA tile: 32, or 16 where 32-row blocks would
+// give a launch fewer than eight waves of resident blocks (about four per SM):
+// on small strips the idle SMs of the last wave then cost more than the
+// smaller blocks' set-up.
+int default_rows(const std::vector<GatherTask> &tasks) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+        sms = 152;
+    uint64_t blocks = 0;
+    for (auto &t : tasks) blocks += (t.rows + 31) / 32;
+    return blocks >= 8ull * 4 * (uint64_t)sms ? 32 : 16;
+}
+
 uint32_t assign_blocks(std::vector<GatherTask> &tasks, int items) {
     uint32_t blk = 0;
     for (auto &t : tasks) {

@@ -246,7 +246,7 @@ static int launch_batch(cp_server *sv, std::vector<GatherTask> &tasks) {
     int tile_a = 0, tile_b = kGatherItems;
     uint32_t blk_a = 0, blk_b = 0;
     if (!a.empty()) {
-        tile_a = effective_tile(a, make_tile(32, 0, 0, 0));
+        tile_a = effective_tile(a, make_tile(default_rows(a), 0, 0, 0));
         blk_a = assign_blocks(a, tile_a);
     }
     if (!b.empty()) blk_b = assign_blocks(b, tile_b);

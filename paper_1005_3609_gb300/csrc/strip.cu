@@ -169,7 +169,7 @@ static int make_strip(std::shared_ptr<TableSet> tabs, int lattice, int L, const 
     {
         std::vector<GatherTask> probe;
         append_gather_tasks(&probe, ts.row[0], s->vec[0], s->vec[1], s->primes_dev, s->D1, s->P);
-        s->tile = effective_tile(probe, make_tile(32, 0, 0, 0));
+        s->tile = effective_tile(probe, make_tile(default_rows(probe), 0, 0, 0));
     }
     // launches of one row (starting from vec[b]) and of the read-out chain from vec[b]
     std::vector<GatherTask> all;
@@ -360,7 +360,8 @@ extern "C" int cp_strip_set_tile(cp_strip *s, int tile) {
                      (ring == 0 || (ring >= 16 && ring <= 192)) && (edges <= 2 || edges == 4 || edges == 8) &&
                      (cpt <= 2 || cpt == 4);
     if (tile != 0 && !reg && !tma) return fail(CP_EINVAL, "bad tile (encoding as for cp_sweep_create)");
-    const int t = effective_tile(s->row_tasks[0][0], tile ? tile : make_tile(32, 0, 0, 0));
+    const int t = effective_tile(s->row_tasks[0][0],
+                                 tile ? tile : make_tile(default_rows(s->row_tasks[0][0]), 0, 0, 0));
     CP_CUDA_TRY(cudaStreamSynchronize(s->stream));
     s->tile = t;
     std::vector<GatherTask> all;
