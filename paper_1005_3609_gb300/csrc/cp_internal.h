@@ -246,7 +246,7 @@ int primes_product_bits(const uint32_t *primes, int P);
 void binomial_bits(uint64_t n_edges, int n_coeffs, uint32_t *bits_out);
 uint64_t rectangle_edges(int lattice, int L, int N);
 // CP_OK if no flag is set, else CP_EPRIMES with a message counting them.
-int crt_verdict(const uint32_t *flags, int n_coeffs);
+int crt_outcome(const uint32_t *flags, int n_coeffs);
 // Load the CRT module (and the static array of cp_crt_static) on the current device.
 int crt_static_touch();
 

@@ -257,7 +257,7 @@ static int crt_host(const char *name, const uint32_t *res, const uint32_t *prime
 }
 
 // Count the flagged coefficients and turn them into CP_EPRIMES.
-int cp::crt_verdict(const uint32_t *flags, int n_coeffs) {
+int cp::crt_outcome(const uint32_t *flags, int n_coeffs) {
     int nb = 0, nu = 0;
     for (int j = 0; j < n_coeffs; ++j) {
         nb += (flags[j] & 1u) ? 1 : 0;
@@ -281,7 +281,7 @@ extern "C" int cp_crt_checked(const uint32_t *res, const uint32_t *primes, int P
     if (rc) return rc;
     if (flags_out)
         for (int j = 0; j < n_coeffs; ++j) flags_out[j] = flags[j];
-    return crt_verdict(flags.data(), n_coeffs);
+    return crt_outcome(flags.data(), n_coeffs);
 }
 
 extern "C" int cp_whitney_bits(int lattice, int L, int N, int n_coeffs, uint32_t *bits_out) {

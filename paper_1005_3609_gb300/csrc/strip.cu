@@ -321,7 +321,7 @@ extern "C" int cp_read_integers(cp_strip *s, uint32_t *limbs_out, size_t limbs_l
     if (flags_out)
         for (int j = 0; j < D1; ++j) flags_out[j] = flags[j];
     if (height_out) *height_out = s->height;
-    return crt_verdict(flags.data(), D1);
+    return crt_outcome(flags.data(), D1);
 }
 
 extern "C" int cp_strip_info(const cp_strip *s, uint64_t n_states[2], int *degree, int *height) {

@@ -489,7 +489,7 @@ extern "C" int cp_sweep_series_integers(cp_sweep *sw, uint32_t *limbs_out, size_
     if ((rc = cp_sweep_sync(sw))) return rc;
     if (flags_out)
         for (size_t j = 0; j < flags.size(); ++j) flags_out[j] = flags[j];
-    return crt_verdict(flags.data(), 3 * n);
+    return crt_outcome(flags.data(), 3 * n);
 }
 
 // The same program without the graph, with an event pair around every batched
