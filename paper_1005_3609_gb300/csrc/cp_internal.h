@@ -103,6 +103,8 @@ struct SiteTable {
     uint32_t *row_ptr = nullptr;  // [n_dst + 1]
     uint32_t *edges = nullptr;    // [nnz]
     uint32_t *block_order = nullptr;  // row blocks by smallest source (GatherTask::block_order), or null
+    uint32_t max_coef_sum = 0;        // largest sum of |coefficient| into one destination (an upper bound)
+    uint32_t max_abs_coef = 0;        // largest |coefficient|
 };
 
 // All tables of one (lattice, L) on one device; shared between strips.
@@ -158,7 +160,7 @@ struct GatherTask {
     uint32_t cw;              // chunks handled (a column range [c0, c0 + cw) of every row)
     uint32_t src_bits;        // edge format of the table
     uint32_t partial;         // 1: the output feeds further gathers only (words may be left in [-p, p))
-    uint32_t pad;
+    uint32_t small_coefs;     // 1: |coefficient| <= 127 and their sum into any destination < 2^15 (TMA kernel)
     // TMA kernel: the order in which its blocks visit the row blocks, for 16,
     // 32, 64 and 128 rows per block one after another (block_order_offset),
     // or null for row-block order
@@ -208,7 +210,7 @@ inline int tile_shape(int tile) { return (tile >> 28) & 3; }
 // (0: the wide block, 8 / CPT).
 __host__ __device__ constexpr int tma_min_blocks(int E, int CPT, int W = 0) {
     return W == kTmaNarrowWarps ? 4
-                                : (CPT == 1 ? (E >= 8 ? 3 : 4) : (CPT == 2 ? 4 : (E >= 4 ? 4 : 5)));
+                                : (CPT == 1 ? (E >= 2 ? 3 : 4) : (CPT == 2 ? 4 : (E >= 4 ? 4 : 5)));
 }
 __host__ __device__ constexpr int tma_ring_kb_for(int E, int CPT, int W = 0) {
     return W == kTmaNarrowWarps ? 52
@@ -221,6 +223,12 @@ uint32_t task_blocks(const GatherTask &t, int items);
 uint32_t assign_blocks(std::vector<GatherTask> &tasks, int items);
 // Effective tile for a batch (falls back from TMA to the register kernel when needed).
 int effective_tile(const std::vector<GatherTask> &tasks, int items);
+// The TMA kernel accumulates coef * x as two 16 x 8-bit dot products into 32-bit
+// halves (gather_tma.cu), exact while |coef| <= kTmaMaxCoef and the sum of
+// |coef| into any destination stays below kTmaMaxCoefSum; other tables use the
+// register kernel.
+constexpr uint32_t kTmaMaxCoef = 127;
+constexpr uint32_t kTmaMaxCoefSum = 1u << 15;
 // Rows per block of the default TMA tile for a launch of these tasks (16 or 32).
 int default_rows(const std::vector<GatherTask> &tasks);
 // Launch a batch of tasks (tasks_dev = device copy, block_begin assigned for `items`).

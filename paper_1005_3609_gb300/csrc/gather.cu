@@ -235,6 +235,7 @@ void append_gather_tasks(std::vector<GatherTask> *tasks, const SiteTable &tab, c
     t.src_bits = (uint32_t)tab.op.src_bits;
     t.block_order = tab.block_order;
     t.partial = partial ? 1u : 0u;
+    t.small_coefs = (tab.max_abs_coef <= kTmaMaxCoef && tab.max_coef_sum < kTmaMaxCoefSum) ? 1u : 0u;
     const uint32_t ncol = v4 ? (t.C + 255) / 256 : 1;
     for (uint32_t k = 0; k < ncol; ++k) {  // balanced column ranges
         t.c0 = (uint32_t)((uint64_t)t.C * k / ncol);

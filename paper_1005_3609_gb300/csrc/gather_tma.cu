@@ -22,7 +22,9 @@
 // W = 5 at CPT 1 (a narrow block for rows of 129..160 chunks, one group);
 // warps whose chunks all lie beyond the row leave at once.  Per stage a
 // consumer reads the E coefficients, then edge by edge its chunks of the slots,
-// adding coef * chunk into signed 64-bit accumulators, and releases the stage;
+// adding coef * chunk into pairs of 32-bit sums (two 16 x 8-bit dot products
+// per word; tables with |coef| > 127 or coefficient sums of 2^15 and more use
+// the register kernel), and releases the stage;
 // when the CSR reaches the end of a destination row the thread reduces its four
 // words modulo their primes (integer Barrett, modred.cuh) and streams them out.
 //
@@ -147,7 +149,8 @@ __device__ __forceinline__ void tma_produce(const GatherTask &t, const TmaBlock 
                 const uint32_t slot = st * E + j;
                 if (idx < gn) {
                     const uint32_t sh = (q >> t.src_bits) & 3u;
-                    S.cf[slot] = (int)q >> (t.src_bits + 2);
+                    const uint32_t cb = (uint32_t)((int)q >> (t.src_bits + 2)) & 0xFFu;
+                    S.cf[slot] = (int)(cb | (cb << 24));  // coefficient in bytes 0 and 3 (see mad_dp2a)
                     S.sh[slot] = sh;
                     const uint32_t back = sh * t.cpd;  // shift in chunks
                     const uint32_t skip = back > t.c0 ? min(back - t.c0, t.cw) : 0u;
@@ -206,9 +209,26 @@ __device__ __forceinline__ uint4 lds128(uint32_t addr) {
     asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
     return v;
 }
-// acc += a * b with a, b signed 32-bit (one widening multiply-add).
-__device__ __forceinline__ void mad_wide(long long &acc, uint32_t a, int b) {
-    asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(a), "r"(b));
+// Exact sums without 64-bit multiply-adds.  An input word x (a residue in
+// [0, p) or a signed representative in [-p, p), as 32-bit two's complement)
+// is x = xh 2^16 + xl with xl = x & 0xffff (unsigned) and xh = x >> 16
+// (signed).  The edge's coefficient c (|c| <= 127) sits in bytes 0 and 3 of b,
+// so dp2a.lo (x's halves times b's bytes 0, 1) adds c xl and dp2a.hi (times
+// bytes 2, 3) adds c xh, each into a 32-bit sum: with S = sum |c| < 2^15 over
+// the destination's edges, |lo| <= S (2^16 - 1) < 2^31 and |hi| <= S 2^15 <
+// 2^31, and sum_e c_e x_e = hi 2^16 + lo exactly.  Two 32-bit instructions
+// per word and edge where a widening 64-bit multiply-add costs about three.
+struct Acc2 {
+    int lo, hi;
+};
+__device__ __forceinline__ void mad_dp2a(Acc2 &acc, uint32_t x, int b) {
+    asm("dp2a.lo.u32.s32 %0, %2, %3, %0;\n\tdp2a.hi.s32.s32 %1, %2, %3, %1;"
+        : "+r"(acc.lo), "+r"(acc.hi)
+        : "r"(x), "r"(b));
+}
+// The accumulator the reduction takes: p 2^21 + sum_e c_e x_e (modred.cuh).
+__device__ __forceinline__ long long acc_value(const Acc2 &a, uint32_t p) {
+    return modred_bias(p) + ((long long)a.hi << 16) + a.lo;
 }
 // Arrive on an mbarrier from the lanes where pred != 0, without branching.
 __device__ __forceinline__ void mbar_arrive_if(uint32_t a, uint32_t pred) {
@@ -266,16 +286,12 @@ __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock 
     uint4 *out = reinterpret_cast<uint4 *>(t.out) + (size_t)bk.row0 * t.C;
     const uint32_t C = t.C;
     const uint32_t gNS = g * bk.NS;
-    long long a[CPT][4];
+    Acc2 a[CPT][4];
     auto reset = [&]() {
 #pragma unroll
-        for (int k = 0; k < CPT; ++k) {
-            const uint4 p = (k == 0 || same_primes) ? P0 : *reinterpret_cast<const uint4 *>(S.p + pcs[k]);
-            a[k][0] = modred_bias(p.x);
-            a[k][1] = modred_bias(p.y);
-            a[k][2] = modred_bias(p.z);
-            a[k][3] = modred_bias(p.w);
-        }
+        for (int k = 0; k < CPT; ++k)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) a[k][w] = Acc2{0, 0};
     };
     uint32_t r = r0;
     auto flush = [&]() {
@@ -288,12 +304,14 @@ __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock 
                 sh = *reinterpret_cast<const uint4 *>(S.s + pcs[k]);
             }
             const uint4 v =
-                FULL ? make_uint4(modred_reduce(a[k][0], p.x, m.x, sh.x), modred_reduce(a[k][1], p.y, m.y, sh.y),
-                                  modred_reduce(a[k][2], p.z, m.z, sh.z), modred_reduce(a[k][3], p.w, m.w, sh.w))
-                     : make_uint4(modred_reduce_signed(a[k][0], p.x, m.x, sh.x),
-                                  modred_reduce_signed(a[k][1], p.y, m.y, sh.y),
-                                  modred_reduce_signed(a[k][2], p.z, m.z, sh.z),
-                                  modred_reduce_signed(a[k][3], p.w, m.w, sh.w));
+                FULL ? make_uint4(modred_reduce(acc_value(a[k][0], p.x), p.x, m.x, sh.x),
+                                  modred_reduce(acc_value(a[k][1], p.y), p.y, m.y, sh.y),
+                                  modred_reduce(acc_value(a[k][2], p.z), p.z, m.z, sh.z),
+                                  modred_reduce(acc_value(a[k][3], p.w), p.w, m.w, sh.w))
+                     : make_uint4(modred_reduce_signed(acc_value(a[k][0], p.x), p.x, m.x, sh.x),
+                                  modred_reduce_signed(acc_value(a[k][1], p.y), p.y, m.y, sh.y),
+                                  modred_reduce_signed(acc_value(a[k][2], p.z), p.z, m.z, sh.z),
+                                  modred_reduce_signed(acc_value(a[k][3], p.w), p.w, m.w, sh.w));
             stcs128_if(out + (size_t)r * C + gcs[k], v, active[k]);
         }
         ++r;
@@ -333,10 +351,10 @@ __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock 
             for (int k = 0; k < CPT; ++k) {
                 const uint32_t addr = col[k] + so + j * RB;
                 const uint4 x = (PRED && k == 0) ? lds128_if(addr, deg0 >= S.sh[slot0 + j] ? 1u : 0u) : lds128(addr);
-                mad_wide(a[k][0], x.x, f[j]);
-                mad_wide(a[k][1], x.y, f[j]);
-                mad_wide(a[k][2], x.z, f[j]);
-                mad_wide(a[k][3], x.w, f[j]);
+                mad_dp2a(a[k][0], x.x, f[j]);
+                mad_dp2a(a[k][1], x.y, f[j]);
+                mad_dp2a(a[k][2], x.z, f[j]);
+                mad_dp2a(a[k][3], x.w, f[j]);
             }
             if (base + j + 1 == rend) {  // the last edge of row r (empty slots past gn never match)
                 flush();
@@ -433,7 +451,7 @@ __global__ void __launch_bounds__(tma_threads(W), tma_min_blocks(E, CPT, W == kT
 constexpr uint32_t kTmaRingMax = 192 * 1024;
 constexpr uint32_t kTmaRingMin = 16 * 1024;
 
-bool tma_usable(const GatherTask &t) { return t.vec4 && t.cw >= 1 && t.cw <= 256; }
+bool tma_usable(const GatherTask &t) { return t.vec4 && t.cw >= 1 && t.cw <= 256 && t.small_coefs; }
 
 template <int E, int CPT, int W>
 static int set_attr() {

@@ -270,15 +270,20 @@ __global__ void build_terms_kernel(OpDesc op, const RankTables *Tg, uint32_t *sl
 
 // Edges per destination, and sum of |coef| per destination into csum.
 __global__ void count_kernel(const uint32_t *slot_dst, const uint32_t *slot_edge, uint64_t n_slots, int src_bits,
-                             uint32_t *cnt, uint32_t *csum) {
+                             uint32_t *cnt, uint32_t *csum, int *max_coef) {
+    uint32_t m = 0;  // largest |coefficient| seen by this thread
     for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n_slots;
          k += (uint64_t)gridDim.x * blockDim.x) {
         uint32_t d = slot_dst[k];
         if (d == ~0u) continue;
         atomicAdd(&cnt[d], 1u);
         const int c = (int)slot_edge[k] >> (src_bits + 2);
-        atomicAdd(&csum[d], (uint32_t)(c < 0 ? -c : c));
+        const uint32_t a = (uint32_t)(c < 0 ? -c : c);
+        atomicAdd(&csum[d], a);
+        m = max(m, a);
     }
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(max_coef, (int)m);
 }
 
 // Largest entry of cnt (warp maximum, one atomic per warp).
@@ -523,7 +528,7 @@ static int build_table(const OpDesc &op, const RankTables *T_dev, cudaStream_t s
     if ((rc = dev_alloc((void **)&slot_dst, n_slots * 4)) || (rc = dev_alloc((void **)&slot_edge, n_slots * 4)) ||
         (rc = dev_alloc((void **)&cnt, op.out.size * 4)) || (rc = dev_alloc((void **)&cursor, op.out.size * 4)) ||
         (rc = dev_alloc((void **)&csum, op.out.size * 4)) ||
-        (rc = dev_alloc((void **)&err, 2 * sizeof(int)))) {
+        (rc = dev_alloc((void **)&err, 3 * sizeof(int)))) {
         cleanup();
         return rc;
     }
@@ -534,7 +539,7 @@ static int build_table(const OpDesc &op, const RankTables *T_dev, cudaStream_t s
     cudaMemsetAsync(cnt, 0, op.out.size * 4, st);
     cudaMemsetAsync(cursor, 0, op.out.size * 4, st);
     cudaMemsetAsync(csum, 0, op.out.size * 4, st);
-    cudaMemsetAsync(err, 0, 2 * sizeof(int), st);
+    cudaMemsetAsync(err, 0, 3 * sizeof(int), st);
     const int bt = 128;
     if (op.fused)
         build_terms_kernel<kMaxFused><<<(unsigned)((op.in.size + bt - 1) / bt), bt, 0, st>>>(op, T_dev, slot_dst,
@@ -542,7 +547,7 @@ static int build_table(const OpDesc &op, const RankTables *T_dev, cudaStream_t s
     else
         build_terms_kernel<kMaxTerms><<<(unsigned)((op.in.size + bt - 1) / bt), bt, 0, st>>>(op, T_dev, slot_dst,
                                                                                             slot_edge, K, err);
-    count_kernel<<<1216, 256, 0, st>>>(slot_dst, slot_edge, n_slots, op.src_bits, cnt, csum);
+    count_kernel<<<1216, 256, 0, st>>>(slot_dst, slot_edge, n_slots, op.src_bits, cnt, csum, err + 2);
     max_count_kernel<<<608, 256, 0, st>>>(csum, op.out.size, err + 1);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -553,9 +558,9 @@ static int build_table(const OpDesc &op, const RankTables *T_dev, cudaStream_t s
         cleanup();
         return rc;
     }
-    int herr[2] = {0, 0};
+    int herr[3] = {0, 0, 0};
     uint32_t nnz = 0;
-    cudaMemcpyAsync(herr, err, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(herr, err, 3 * sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(&nnz, tab->row_ptr + op.out.size, 4, cudaMemcpyDeviceToHost, st);
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
@@ -580,6 +585,8 @@ static int build_table(const OpDesc &op, const RankTables *T_dev, cudaStream_t s
                                    std::to_string(op.i));
     }
     tab->nnz = nnz;
+    tab->max_coef_sum = (uint32_t)herr[1];
+    tab->max_abs_coef = (uint32_t)herr[2];
     if ((rc = dev_alloc((void **)&tab->edges, (size_t)(nnz ? nnz : 1) * 4))) {
         cleanup();
         return rc;
@@ -617,6 +624,7 @@ static int identity_table(int m, SiteTable *tab) {
     op.out = op.in;
     tab->op = op;
     tab->n_src = tab->n_dst = tab->nnz = tab->n_site_out = 1;
+    tab->max_coef_sum = tab->max_abs_coef = 1;
     int rc = dev_alloc((void **)&tab->row_ptr, 8);
     if (rc) return rc;
     if ((rc = dev_alloc((void **)&tab->edges, 4))) return rc;
