@@ -94,6 +94,8 @@ struct TmaShared {
     alignas(16) uint32_t p[CP_MAX_PRIMES];  // reduction constants per prime
     alignas(16) uint32_t m[CP_MAX_PRIMES];
     alignas(16) uint32_t s[CP_MAX_PRIMES];
+    alignas(16) uint32_t l0[CP_MAX_PRIMES];  // start of a word's sums: lo = (p & 1) 2^15, hi = p >> 1,
+    alignas(16) uint32_t h0[CP_MAX_PRIMES];  // so that hi 2^16 + lo starts at B = p 2^15
     uint32_t rp[kTmaMaxRows + 1];           // the block's row pointers
     long long deadline;            // clock64 limit of every wait
     GatherTask task;               // the block's task (read where needed, not held in registers)
@@ -215,9 +217,11 @@ __device__ __forceinline__ uint4 lds128(uint32_t addr) {
 // (signed).  The edge's coefficient c (|c| <= 127) sits in bytes 0 and 3 of b,
 // so dp2a.lo (x's halves times b's bytes 0, 1) adds c xl and dp2a.hi (times
 // bytes 2, 3) adds c xh, each into a 32-bit sum: with S = sum |c| < 2^15 over
-// the destination's edges, |lo| <= S (2^16 - 1) < 2^31 and |hi| <= S 2^15 <
-// 2^31, and sum_e c_e x_e = hi 2^16 + lo exactly.  Two 32-bit instructions
-// per word and edge where a widening 64-bit multiply-add costs about three.
+// the destination's edges and the starting values below (lo <= 2^15, hi <
+// 2^30), |lo| <= 2^15 + S (2^16 - 1) < 2^31 and |hi| < 2^30 + S 2^15 < 2^31,
+// and hi 2^16 + lo is the start plus sum_e c_e x_e, exactly.  Two 32-bit
+// instructions per word and edge where a widening 64-bit multiply-add costs
+// about three.
 struct Acc2 {
     int lo, hi;
 };
@@ -226,7 +230,21 @@ __device__ __forceinline__ void mad_dp2a(Acc2 &acc, uint32_t x, int b) {
         : "+r"(acc.lo), "+r"(acc.hi)
         : "r"(x), "r"(b));
 }
-// The accumulator the reduction takes: p 2^21 + sum_e c_e x_e (modred.cuh).
+// The sums start at B = p 2^15 (a multiple of p above |sum_e c_e x_e| <= S p),
+// so u = hi 2^16 + lo = B + sum_e c_e x_e lies in (0, p 2^16).
+//
+// u mod p for primes p >= 2^17 in 32-bit arithmetic: the quotient estimate of
+// modred.cuh with s = b - 2 >= 16 takes h = floor(u / 2^s) = floor((hi +
+// floor(lo / 2^16)) / 2^(s-16)) (c = s - 16); as u < 2^(b+16) the error terms
+// stay below 2^-14 + 1/2, so r = u - q p (taken modulo 2^32, with u's low word
+// hi 2^16 + lo) lies in [0, 2p).  Returns r reduced (full) or r - p.
+__device__ __forceinline__ uint32_t reduce_halves(const Acc2 &a, uint32_t p, uint32_t m, uint32_t c, bool full) {
+    const uint32_t h = (uint32_t)(a.hi + (a.lo >> 16)) >> c;
+    const uint32_t q = __umulhi(h, m);
+    const uint32_t r = ((uint32_t)a.hi << 16) + (uint32_t)a.lo - q * p;
+    return full ? min(r, r - p) : r - p;
+}
+// Any prime: p 2^21 + u as the accumulator of modred.cuh.
 __device__ __forceinline__ long long acc_value(const Acc2 &a, uint32_t p) {
     return modred_bias(p) + ((long long)a.hi << 16) + a.lo;
 }
@@ -256,7 +274,7 @@ __device__ __forceinline__ void stcs128_if(uint4 *ptr, uint4 v, uint32_t pred) {
 // and not stored.  PRED: the warp holds chunks of degree < kTmaMaxShift (only
 // the first chunk can), where a shifted copy leaves the slot's low chunks
 // unwritten and the shift must be checked.
-template <int E, int CPT, bool PRED, bool FULL>
+template <int E, int CPT, bool PRED, bool FULL, bool FR>
 __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock &bk, TmaShared &S, uint32_t ring_addr,
                                             uint32_t g, uint32_t c, uint32_t stride, int *err) {
     const uint32_t lane = threadIdx.x & 31;
@@ -278,7 +296,13 @@ __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock 
     const bool same_primes = stride % t.cpd == 0;
     const uint4 P0 = *reinterpret_cast<const uint4 *>(S.p + pcs[0]);
     const uint4 M0 = *reinterpret_cast<const uint4 *>(S.m + pcs[0]);
-    const uint4 S0 = *reinterpret_cast<const uint4 *>(S.s + pcs[0]);
+    uint4 S0 = *reinterpret_cast<const uint4 *>(S.s + pcs[0]);
+    uint4 L0 = make_uint4(0, 0, 0, 0), H0 = make_uint4(0, 0, 0, 0);  // starting sums (FR), in registers
+    if (FR) {
+        S0 = make_uint4(S0.x - 16, S0.y - 16, S0.z - 16, S0.w - 16);  // c = s - 16 of reduce_halves
+        L0 = *reinterpret_cast<const uint4 *>(S.l0 + pcs[0]);
+        H0 = *reinterpret_cast<const uint4 *>(S.h0 + pcs[0]);
+    }
     uint32_t r0, r1;
     tma_group_rows(bk, g, &r0, &r1);
     const uint32_t gb = S.rp[r0], gn = S.rp[r1] - gb;
@@ -289,9 +313,18 @@ __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock 
     Acc2 a[CPT][4];
     auto reset = [&]() {
 #pragma unroll
-        for (int k = 0; k < CPT; ++k)
-#pragma unroll
-            for (int w = 0; w < 4; ++w) a[k][w] = Acc2{0, 0};
+        for (int k = 0; k < CPT; ++k) {
+            const bool own = k == 0 || same_primes;
+            uint4 l = make_uint4(0, 0, 0, 0), h = l;  // zero sums unless FR
+            if (FR) {
+                l = own ? L0 : *reinterpret_cast<const uint4 *>(S.l0 + pcs[k]);
+                h = own ? H0 : *reinterpret_cast<const uint4 *>(S.h0 + pcs[k]);
+            }
+            a[k][0] = Acc2{(int)l.x, (int)h.x};
+            a[k][1] = Acc2{(int)l.y, (int)h.y};
+            a[k][2] = Acc2{(int)l.z, (int)h.z};
+            a[k][3] = Acc2{(int)l.w, (int)h.w};
+        }
     };
     uint32_t r = r0;
     auto flush = [&]() {
@@ -302,8 +335,11 @@ __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock 
                 p = *reinterpret_cast<const uint4 *>(S.p + pcs[k]);
                 m = *reinterpret_cast<const uint4 *>(S.m + pcs[k]);
                 sh = *reinterpret_cast<const uint4 *>(S.s + pcs[k]);
+                if (FR) sh = make_uint4(sh.x - 16, sh.y - 16, sh.z - 16, sh.w - 16);
             }
             const uint4 v =
+                FR ? make_uint4(reduce_halves(a[k][0], p.x, m.x, sh.x, FULL), reduce_halves(a[k][1], p.y, m.y, sh.y, FULL),
+                                  reduce_halves(a[k][2], p.z, m.z, sh.z, FULL), reduce_halves(a[k][3], p.w, m.w, sh.w, FULL)) :
                 FULL ? make_uint4(modred_reduce(acc_value(a[k][0], p.x), p.x, m.x, sh.x),
                                   modred_reduce(acc_value(a[k][1], p.y), p.y, m.y, sh.y),
                                   modred_reduce(acc_value(a[k][2], p.z), p.z, m.z, sh.z),
@@ -371,6 +407,18 @@ __device__ __forceinline__ void tma_consume(const GatherTask &t, const TmaBlock 
     }
 }
 
+template <int E, int CPT, bool FR>
+__device__ __forceinline__ void tma_dispatch(const GatherTask &t, const TmaBlock &bk, TmaShared &S, uint32_t ring_addr,
+                                             uint32_t g, uint32_t c, uint32_t stride, int *err, bool pred) {
+    if (t.partial) {
+        if (pred) tma_consume<E, CPT, true, false, FR>(t, bk, S, ring_addr, g, c, stride, err);
+        else tma_consume<E, CPT, false, false, FR>(t, bk, S, ring_addr, g, c, stride, err);
+    } else {
+        if (pred) tma_consume<E, CPT, true, true, FR>(t, bk, S, ring_addr, g, c, stride, err);
+        else tma_consume<E, CPT, false, true, FR>(t, bk, S, ring_addr, g, c, stride, err);
+    }
+}
+
 __host__ __device__ constexpr int tma_threads(int W) { return 32 * (1 + W); }
 
 // W consumer warps: 8 / CPT (the wide block, 256 chunks per block) or
@@ -416,6 +464,8 @@ __global__ void __launch_bounds__(tma_threads(W), tma_min_blocks(E, CPT, W == kT
         S.p[threadIdx.x] = mr.p;
         S.m[threadIdx.x] = mr.m;
         S.s[threadIdx.x] = mr.s;
+        S.l0[threadIdx.x] = (mr.p & 1u) << 15;
+        S.h0[threadIdx.x] = mr.p >> 1;
     }
     if (threadIdx.x == 0) {
         for (uint32_t s = 0; s < bk.G * bk.NS; ++s) {
@@ -425,7 +475,10 @@ __global__ void __launch_bounds__(tma_threads(W), tma_min_blocks(E, CPT, W == kT
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         S.deadline = clock64() + kWaitCycles;
     }
-    __syncthreads();
+    // one chunk per thread and every prime at least 2^17: the consumers start the sums at
+    // p 2^15 and reduce in 32-bit arithmetic (reduce_halves); otherwise from zero, in 64 bits
+    const bool fr =
+        __syncthreads_and(threadIdx.x >= t.n_primes || S.p[threadIdx.x] >= (1u << 17)) != 0 && CPT == 1;
     const uint32_t warp = threadIdx.x >> 5;
     if (warp == 0) {
         tma_produce<E>(t, bk, S, ring, err);
@@ -438,13 +491,10 @@ __global__ void __launch_bounds__(tma_threads(W), tma_min_blocks(E, CPT, W == kT
     const uint32_t stride = 32 * wpg;  // chunks the group's warps cover side by side
     const uint32_t ring_addr = smem_addr(ring);
     const bool pred = t.c0 + wi * 32 < (uint32_t)kTmaMaxShift * t.cpd;
-    if (t.partial) {
-        if (pred) tma_consume<E, CPT, true, false>(t, bk, S, ring_addr, g, c, stride, err);
-        else tma_consume<E, CPT, false, false>(t, bk, S, ring_addr, g, c, stride, err);
-    } else {
-        if (pred) tma_consume<E, CPT, true, true>(t, bk, S, ring_addr, g, c, stride, err);
-        else tma_consume<E, CPT, false, true>(t, bk, S, ring_addr, g, c, stride, err);
-    }
+    if (fr)
+        tma_dispatch<E, CPT, (CPT == 1)>(t, bk, S, ring_addr, g, c, stride, err, pred);
+    else
+        tma_dispatch<E, CPT, false>(t, bk, S, ring_addr, g, c, stride, err, pred);
 }
 
 // Ring sizes: ring_kb KB per block (several blocks per SM).

@@ -246,6 +246,20 @@ def test_strip_tiles_agree():
             s.set_tile(32 | (3 << 28))  # no block shape 3
 
 
+@pytest.mark.parametrize("primes", [[3, 5, 7, 65521], [2, 131071, 2147483629, 2147483587],
+                                    [131101, 131111, 2147483647, 1073741827]])
+def test_small_and_large_primes_on_the_bulk_copy_kernel(primes):
+    # four primes per 16-byte chunk (the TMA kernel); primes below 2^17 take the
+    # 64-bit reduction of the word sums, all primes >= 2^17 the 32-bit one
+    for lattice in ("square", "triangular"):
+        want = gpu_util.residues_of(tm_exact.ptilde(lattice, 6, 6), primes)
+        for tile in (0, 32 | (2 << 24), 16 | (8 << 20)):
+            with cp.Strip(lattice, 6, primes, max_degree=-1, max_rows=6) as s:
+                s.set_tile(tile)
+                s.advance(5)
+                assert s.read().tolist() == want, (lattice, hex(tile))
+
+
 @pytest.mark.parametrize("lattice", ["square", "triangular"])
 def test_narrow_blocks_match_oracle(lattice):
     # 6 x 6 at full degree with 16 primes: rows of 36 degrees x 4 chunks = 144
