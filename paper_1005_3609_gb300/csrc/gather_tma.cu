@@ -475,10 +475,11 @@ __global__ void __launch_bounds__(tma_threads(W), tma_min_blocks(E, CPT, W == kT
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         S.deadline = clock64() + kWaitCycles;
     }
-    // one chunk per thread and every prime at least 2^17: the consumers start the sums at
-    // p 2^15 and reduce in 32-bit arithmetic (reduce_halves); otherwise from zero, in 64 bits
+    // every prime at least 2^17: the consumers start the sums at p 2^15 and reduce in
+    // 32-bit arithmetic (reduce_halves); otherwise from zero, in 64 bits (the two paths are
+    // separate instantiations: one kernel body holding both ran slower)
     const bool fr =
-        __syncthreads_and(threadIdx.x >= t.n_primes || S.p[threadIdx.x] >= (1u << 17)) != 0 && CPT == 1;
+        __syncthreads_and(threadIdx.x >= t.n_primes || S.p[threadIdx.x] >= (1u << 17)) != 0;
     const uint32_t warp = threadIdx.x >> 5;
     if (warp == 0) {
         tma_produce<E>(t, bk, S, ring, err);
@@ -492,7 +493,7 @@ __global__ void __launch_bounds__(tma_threads(W), tma_min_blocks(E, CPT, W == kT
     const uint32_t ring_addr = smem_addr(ring);
     const bool pred = t.c0 + wi * 32 < (uint32_t)kTmaMaxShift * t.cpd;
     if (fr)
-        tma_dispatch<E, CPT, (CPT == 1)>(t, bk, S, ring_addr, g, c, stride, err, pred);
+        tma_dispatch<E, CPT, true>(t, bk, S, ring_addr, g, c, stride, err, pred);
     else
         tma_dispatch<E, CPT, false>(t, bk, S, ring_addr, g, c, stride, err, pred);
 }
