@@ -427,6 +427,17 @@ int cp_debug_wait_timeout(long long cycles);
  * otherwise.  Synchronous. */
 int cp_debug_reduce(const int64_t *v_host, const uint32_t *p_host, int n, uint32_t *out_host);
 
+/* The 32-bit reduction of the bulk-copy gather (Sec. 3.5), which it uses when
+ * every prime of a launch is at least 2^17: a word's sum is kept as two
+ * 32-bit halves, u = hi_host[k] 2^16 + lo_host[k], and reduced from them with
+ * 32-bit operations.  out_host[k] = u mod p_host[k] in [0, p) when full != 0,
+ * else (u mod p) or (u mod p) - p, a signed representative in [-p, p) as the
+ * kernel stores for outputs that only feed further gathers.  Requires
+ * 2^17 <= p_host[k] < 2^31 and 0 < u < p_host[k] 2^16; CP_EINVAL otherwise.
+ * A diagnostic (it allocates device buffers).  Synchronous. */
+int cp_debug_reduce_halves(const int32_t *lo_host, const int32_t *hi_host, const uint32_t *p_host, int n, int full,
+                           uint32_t *out_host);
+
 /* One chromatic transfer-matrix table as the kernels use it (CSR by
  * destination): paired = 1 for the square lattice's two-site tables; which = 0
  * for the row factors (index 0 = T_1, or T_2 T_1 when paired), 1 for the

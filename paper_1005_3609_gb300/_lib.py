@@ -75,6 +75,8 @@ SIGNATURES = {
     "cp_debug_table": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, u32p,
                                       ctypes.c_uint64, u32p, ctypes.c_uint64, u64p]),
     "cp_debug_reduce": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64), u32p, ctypes.c_int, u32p]),
+    "cp_debug_reduce_halves": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), u32p,
+                                              ctypes.c_int, ctypes.c_int, u32p]),
     "cp_server_stats": (ctypes.c_int, [vp, u64p, u64p, u64p, ctypes.POINTER(ctypes.c_size_t)]),
     "cp_server_destroy": (None, [vp]),
     "cp_crt": (ctypes.c_int, [u32p, u32p, ctypes.c_int, ctypes.c_int, u32p, ctypes.c_int]),
@@ -313,6 +315,21 @@ def debug_reduce(values, primes):
     check("cp_debug_reduce", load().cp_debug_reduce(v.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), pp, len(v),
                                                     out.ctypes.data_as(u32p)))
     return [int(x) for x in out]
+
+
+def debug_reduce_halves(lo, hi, primes, full=True):
+    """The bulk-copy gather's 32-bit reduction of u = hi 2^16 + lo on the GPU
+    (cp_debug_reduce_halves): u mod p, or a representative in [-p, p) (as
+    signed ints) when full is False."""
+    lo_a = np.ascontiguousarray(np.asarray(lo, dtype=np.int32))
+    hi_a = np.ascontiguousarray(np.asarray(hi, dtype=np.int32))
+    p, pp = _u32(primes)
+    out = np.zeros(len(lo_a), dtype=np.uint32)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    check("cp_debug_reduce_halves", load().cp_debug_reduce_halves(lo_a.ctypes.data_as(i32p), hi_a.ctypes.data_as(i32p),
+                                                                  pp, len(lo_a), 1 if full else 0,
+                                                                  out.ctypes.data_as(u32p)))
+    return [int(x) for x in (out if full else out.view(np.int32))]
 
 
 def debug_table(lattice, L, paired, which, index):

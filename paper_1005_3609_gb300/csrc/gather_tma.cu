@@ -592,3 +592,50 @@ int launch_gather_tma(const GatherTask *tasks_dev, int n_tasks, uint32_t total_b
 }
 
 }  // namespace cp
+
+// Diagnostic: reduce_halves on given word sums (one thread per value).
+namespace cp {
+__global__ void debug_halves_kernel(const int *lo, const int *hi, const uint32_t *pr, int n, int full, uint32_t *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const ModRed mr = modred_make(pr[k]);
+    out[k] = reduce_halves(Acc2{lo[k], hi[k]}, mr.p, mr.m, mr.s - 16, full != 0);
+}
+}  // namespace cp
+
+extern "C" int cp_debug_reduce_halves(const int32_t *lo_host, const int32_t *hi_host, const uint32_t *p_host, int n,
+                                      int full, uint32_t *out_host) {
+    using namespace cp;
+    if (n < 0 || (n > 0 && (!lo_host || !hi_host || !p_host || !out_host))) return fail(CP_EINVAL, "bad arguments");
+    for (int k = 0; k < n; ++k) {
+        const uint32_t p = p_host[k];
+        if (p < (1u << 17) || p >= (1u << 31)) return fail(CP_EINVAL, "p must be in [2^17, 2^31)");
+        const long long u = (long long)hi_host[k] * 65536 + lo_host[k];
+        if (u <= 0 || u >= (long long)p * 65536) return fail(CP_EINVAL, "hi 2^16 + lo must lie in (0, p 2^16)");
+    }
+    if (n == 0) return CP_OK;
+    int *lo_d = nullptr, *hi_d = nullptr;
+    uint32_t *p_d = nullptr, *o_d = nullptr;
+    int rc = dev_alloc((void **)&lo_d, 4ull * n);
+    if (!rc) rc = dev_alloc((void **)&hi_d, 4ull * n);
+    if (!rc) rc = dev_alloc((void **)&p_d, 4ull * n);
+    if (!rc) rc = dev_alloc((void **)&o_d, 4ull * n);
+    cudaError_t e = cudaSuccess;
+    if (!rc) {
+        e = cudaMemcpy(lo_d, lo_host, 4ull * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(hi_d, hi_host, 4ull * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(p_d, p_host, 4ull * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            debug_halves_kernel<<<(n + 255) / 256, 256>>>(lo_d, hi_d, p_d, n, full, o_d);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaMemcpy(out_host, o_d, 4ull * n, cudaMemcpyDeviceToHost);
+    }
+    dev_free(lo_d);
+    dev_free(hi_d);
+    dev_free(p_d);
+    dev_free(o_d);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(CP_ECUDA, std::string("cp_debug_reduce_halves: ") + cudaGetErrorString(e));
+    return CP_OK;
+}
