@@ -8,7 +8,9 @@
 // [state][degree][prime], so a shift by one degree is a shift by n_primes
 // words and, for n_primes % 4 == 0, every access is an aligned 16-byte load
 // that reads four primes of one degree.  The coefficients are exact integers:
-// each term coef * x (x < p < 2^31) is added to a signed 64-bit accumulator and
+// each term coef * x (|x| <= p < 2^31: inputs are residues or the signed
+// representatives in [-p, p) that intermediate launches store) is added to a
+// signed 64-bit accumulator and
 // the sum is reduced modulo p once per word (Sec. 3.5), in integer arithmetic
 // only (modred.cuh).
 //

@@ -1,8 +1,8 @@
 // Exact reduction of a gather accumulator modulo a prime, integer arithmetic only.
 //
-// A destination word accumulates v = sum_e coef_e x_e with |x_e| < p (inputs
+// A destination word accumulates v = sum_e coef_e x_e with |x_e| <= p (inputs
 // are residues in [0, p) or signed representatives in [-p, p)), so
-// |v| < p S where S = sum_e |coef_e| over the destination's edges; the table
+// |v| <= p S where S = sum_e |coef_e| over the destination's edges; the table
 // build refuses any table with S >= 2^20 (kReduceMaxCoefSum).  Arithmetic is
 // modulo primes below 2^31 (Sec. 3.5).
 //
